@@ -1,0 +1,225 @@
+/*
+ * sylv_adi.h - C ABI of the GB300 inexact low-rank Sylvester ADI solver.
+ *
+ * Solves  A X + X B = -f g^*  (paper eq. (sylv)) for large sparse real A (n x n),
+ * B (m x m) and low-rank f (n x r), g (m x r), returning X ~ Z Gamma Y^* by the
+ * inexact LR-ADI iteration (Algorithm 1, M = I, C = I).  Each outer step solves
+ * the shifted systems (A + beta_k I) z_k = w_{k-1} and (B + alpha_k I)^* y_k =
+ * t_{k-1} (eq. (lradi_basic)) with restarted, right-Jacobi-preconditioned
+ * GMRES(m) per column, stopped at the tolerances delta^A_k / r, delta^B_k / r
+ * chosen by the paper's controller (Sec. 3.3: eqs. (ADI_relax1_prak),
+ * (upd_resgap), (ADI_relax2_prak), (simple_tols), (one_side)).  All of it runs
+ * on the GPU; the host only launches work and reads a status word.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: SYLV_OK (0) or a negative SYLV_ERR_* code.  Nothing aborts,
+ *   nothing traps.  sylv_last_error() gives a message for the calling thread.
+ * - Dense blocks are column-major with leading dimension = number of rows.
+ * - Complex numbers are pairs of doubles (re, im), i.e. C99 double complex.
+ * - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Work is enqueued on it; calls that return results to the host synchronise it.
+ * - Input pointers are borrowed for the duration of the call only; objects copy
+ *   what they keep.  Objects own the device memory they allocate and release it
+ *   in their destroy call.
+ * - Indices are 0-based int32; values float64.
+ */
+#ifndef SYLV_ADI_H
+#define SYLV_ADI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SYLV_OK                 0
+#define SYLV_ERR_INVALID       -1   /* bad argument (null pointer, size, CSR structure) */
+#define SYLV_ERR_CUDA          -2   /* a CUDA runtime call failed */
+#define SYLV_ERR_NOMEM         -3   /* device or host allocation failed */
+#define SYLV_ERR_MAXIT         -4   /* kmax outer steps without reaching tau; factors valid */
+#define SYLV_ERR_INNER_STALL   -5   /* an inner solve hit max_inner before its tolerance */
+#define SYLV_ERR_NONFINITE     -6   /* NaN or Inf met in a norm */
+#define SYLV_ERR_NOT_SOLVED    -7   /* results asked for before sylv_adi_solve */
+#define SYLV_ERR_UNSUPPORTED   -8   /* option combination not built */
+
+/* ---- inner-tolerance strategies (Sec. 3.3 and Sec. 4's list of settings) ---- */
+#define SYLV_STRAT_FIXED        0   /* delta^A = delta^B = fixed_tol (Sec. 4, "fixed") */
+#define SYLV_STRAT_NOBL_MID     1   /* eq. (ADI_relax1_prak) + eq. (simple_tols) */
+#define SYLV_STRAT_BL_MID       2   /* eq. (ADI_relax2_prak) + eq. (simple_tols) */
+#define SYLV_STRAT_NOBL_A       3   /* eq. (ADI_relax1_prak) + eq. (one_side): delta^A = delta^A_min */
+#define SYLV_STRAT_BL_A         4   /* eq. (ADI_relax2_prak) + eq. (one_side) */
+#define SYLV_STRAT_NOBL_B       5   /* mirror of eq. (one_side): delta^B = delta^B_min */
+#define SYLV_STRAT_BL_B         6
+
+/* ---- precision of the inner Krylov solves ---- */
+#define SYLV_PREC_FP64          0   /* everything in float64 */
+
+/* Sparse square matrix in CSR form.  Borrowed; copied by the create calls. */
+typedef struct sylv_csr {
+    int32_t n_rows, n_cols;      /* must be equal */
+    int64_t nnz;
+    const int32_t* rowptr;       /* n_rows + 1 entries, rowptr[0] = 0, nondecreasing */
+    const int32_t* colind;       /* nnz entries in [0, n_cols) */
+    const double*  val;          /* nnz entries */
+    int32_t on_device;           /* 0: host pointers, 1: device pointers */
+} sylv_csr;
+
+typedef struct sylv_shift { double re, im; } sylv_shift;
+
+/* Solver options; sylv_opts_default() fills the paper's defaults (Sec. 4):
+ * xi = 1, delta_min = tau/20 (set at create when left <= 0), delta_max = 0.1,
+ * kmax = 50, strategy BL_MID, fixed_tol = tau/20 (when <= 0), GMRES(30),
+ * max_inner = 20000, float64, right Jacobi on. */
+typedef struct sylv_opts {
+    double  xi;                  /* safeguard xi in (0, 1] of eqs. (ADI_relax1/2_prak) */
+    double  dmin_A, dmin_B;      /* eq. (bound_tols) lower clamps; <= 0 means tau/20 */
+    double  dmax_A, dmax_B;      /* eq. (bound_tols) upper clamps */
+    int32_t kmax;                /* maximum number of outer steps (divisor in hat-eps) */
+    int32_t strategy;            /* SYLV_STRAT_* */
+    double  fixed_tol;           /* tolerance of SYLV_STRAT_FIXED; <= 0 means tau/20 */
+    int32_t restart;             /* GMRES restart length m, 1..SYLV_MAX_RESTART */
+    int32_t max_inner;           /* cap on Arnoldi steps per column solve */
+    int32_t precision;           /* SYLV_PREC_* */
+    int32_t jacobi;              /* 1: right preconditioner P = diag(Op) + shift */
+    int32_t bl_clamp;            /* 0: eq. (ADI_relax2_prak) literally, |.|;
+                                    1: max(., 0) in place of |.| (paper silent) */
+    int32_t rows_per_chunk;      /* work-unit size of the vector kernels; 0 = auto */
+} sylv_opts;
+
+#define SYLV_MAX_RESTART 30
+#define SYLV_MAX_RANK    4
+
+typedef struct sylv_info {
+    int32_t status;              /* last solve's status (SYLV_OK or SYLV_ERR_*) */
+    int32_t steps;               /* outer steps taken (k - 1 at exit) */
+    int32_t kr;                  /* columns of Z and Y = steps * r */
+    int32_t is_complex;          /* factors are complex (complex shifts) */
+    double  rel_res_comp;        /* ||w_k t_k^*|| / ||f g^*|| at exit (the stop test) */
+    double  norm_fg;             /* ||f g^*||_2 */
+    int64_t inner_its_A;         /* sum of Arnoldi steps over all A-side column solves */
+    int64_t inner_its_B;
+    int64_t inner_restarts;      /* GMRES cycles over all solves */
+    int32_t stalled_solves;      /* inner solves that hit max_inner */
+    int32_t ticks;               /* device iterations launched (for diagnostics) */
+} sylv_info;
+
+/* Columns of one row of sylv_adi_history() (doubles, row-major). */
+#define SYLV_HIST_COLS 14
+/* k, alpha_re, beta_re, delta_A, delta_B, hat_eps, ||r^A_k||, ||r^B_k||,
+ * its_A, its_B, u_k, v_k, ||w_k t_k^*||/||fg^*||, ||w_{k-1}||              */
+
+typedef struct sylv_handle sylv_handle;
+typedef struct sylv_op sylv_op;
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* sylv_last_error(void);
+
+/* Fill *o with the defaults above.  Returns SYLV_ERR_INVALID for o == NULL. */
+int sylv_opts_default(sylv_opts* o);
+
+/* ------------------------------------------------------------------------ */
+/* Shifted sparse operator (steps a2/a3 of the hot path)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Upload a CSR matrix (or its transpose, transpose = 1) as a device operator.
+ * A matrix whose nonzeros lie on at most 8 fixed diagonals (finite-difference
+ * stencils, Sec. 4 eq. (ex:convdiff)) is stored by diagonals so the product
+ * reads no column indices; any other CSR is kept as CSR.  The main diagonal is
+ * kept for the Jacobi preconditioner.  Errors: SYLV_ERR_INVALID for a
+ * malformed CSR (non-square, rowptr not monotone, column out of range). */
+int sylv_op_create(const sylv_csr* csr, int32_t transpose, sylv_op** out);
+/* Storage format chosen: 1 = by diagonals (*ndiag set), 0 = CSR. */
+int sylv_op_format(const sylv_op* op, int32_t* is_stencil, int32_t* ndiag, int32_t* n);
+/* Y = (Op + sigma I) P^{-1} X for ncols columns (device pointers, n x ncols,
+ * column-major), P = diag(Op) + sigma I when jacobi = 1, else P = I.  This is
+ * the operator of the inner systems of Algorithm 1 (A + beta_k I, or B^T +
+ * conj(alpha_k) I) under right preconditioning (Sec. 3.3).  is_complex = 1
+ * treats X, Y as complex (interleaved) vectors; sigma must be real otherwise. */
+int sylv_op_apply(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+                  const void* X, void* Y, int32_t ncols, void* stream);
+int sylv_op_destroy(sylv_op* op);
+
+/* ------------------------------------------------------------------------ */
+/* One CGS2 orthogonalisation step (step a4)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Given k orthonormal columns V (n x k, device, ld = n) and w (n, device):
+ * h = V^* w, w -= V h, h2 = V^* w, w -= V h2 (classical Gram-Schmidt applied
+ * twice); on return w holds the orthogonalised vector divided by its norm,
+ * h_out (host, k + 1 entries) holds h + h2 followed by the norm.  1 <= k <= 30.
+ * is_complex as for sylv_op_apply; h_out then holds k + 1 complex entries.
+ * The Arnoldi step of the inner GMRES solves uses the same device code. */
+int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out,
+              int32_t is_complex, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched shifted GMRES (steps a2-a7)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Solve (Op + sigma I) x_l = b_l for l = 0..ncols-1 (device, n x ncols), each
+ * column by restarted GMRES(restart) with x0 = 0, right Jacobi when jacobi =
+ * 1, stopping when the Givens residual estimate is <= tol and confirming with
+ * the recomputed true residual ||b_l - (Op + sigma I) x_l|| <= tol (a new cycle
+ * starts otherwise), or after max_iters Arnoldi steps.  The columns run
+ * concurrently in one set of launches.  Outputs (host arrays of ncols):
+ * iters_out (Arnoldi steps), resnorm_out (true residual norms).
+ * Returns SYLV_ERR_INNER_STALL if some column stopped at max_iters.
+ * Optional hist_out (host, ncols x max_iters doubles, may be NULL): the Givens
+ * residual estimate after each Arnoldi step. */
+int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+               const void* B, void* X, int32_t ncols, double tol, int32_t restart,
+               int32_t max_iters, int32_t* iters_out, double* resnorm_out,
+               double* hist_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Inner-tolerance controller (step a1), evaluated by the device code         */
+/* ------------------------------------------------------------------------ */
+
+/* For each of count inputs, in[i*11 + 0..10] = {k, kmax, eps, xi, u_prev,
+ * v_prev, N_w, N_t, fixed_tol, (unused), (unused)}, with clamps from o, write
+ * out[i*3 + 0..2] = {delta^A_k, delta^B_k, hat-eps_k} (host arrays).  Runs
+ * the same device function the solver runs at the start of every step. */
+int sylv_controller_eval(const sylv_opts* o, int32_t count, const double* in, double* out);
+
+/* ------------------------------------------------------------------------ */
+/* Full solver (Algorithm 1)                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Create a solver for A X + X B = -f g^*.
+ * A: n x n, B: m x m (CSR, borrowed, copied).  f: n x r, g: m x r (host,
+ * column-major, real).  alpha[i], beta[i] (i < n_shifts) is the i-th shift
+ * pair, reused cyclically when the iteration runs past n_shifts; complex pairs
+ * must be followed immediately by their conjugate pair.  tol = tau of
+ * Algorithm 1 (stop when ||w t^*|| < tau ||f g^*||).  opts may be NULL.
+ * Allocates all device memory the solve needs (factors for kmax steps, Krylov
+ * bases for the 2r column solves).  Errors: SYLV_ERR_INVALID, SYLV_ERR_NOMEM,
+ * SYLV_ERR_UNSUPPORTED (r > SYLV_MAX_RANK, restart > SYLV_MAX_RESTART). */
+int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const double* g,
+                    int32_t r, const sylv_shift* alpha, const sylv_shift* beta,
+                    int32_t n_shifts, double tol, const sylv_opts* opts, void* stream,
+                    sylv_handle** out);
+/* Replace f and g (same shapes) before the next solve; host pointers. */
+int sylv_adi_set_rhs(sylv_handle* h, const double* f, const double* g);
+/* Same, from device pointers (n x r and m x r float64, column-major). */
+int sylv_adi_set_rhs_device(sylv_handle* h, const double* f, const double* g);
+/* Run Algorithm 1 from w_0 = f, t_0 = g.  Blocks until done; returns the
+ * solve's status (SYLV_OK, SYLV_ERR_MAXIT, SYLV_ERR_INNER_STALL as a warning,
+ * SYLV_ERR_NONFINITE). */
+int sylv_adi_solve(sylv_handle* h);
+int sylv_adi_info(const sylv_handle* h, sylv_info* info);
+/* Per-step metrics, rows of SYLV_HIST_COLS doubles (see above); writes
+ * min(cap, steps) rows to buf and the row count to *rows. */
+int sylv_adi_history(const sylv_handle* h, double* buf, int32_t cap, int32_t* rows);
+/* Copy Z (n x kr), Y (m x kr) and gamma (kr) to caller buffers (host when
+ * on_device = 0, device otherwise).  Complex factors are written as
+ * interleaved pairs.  Any of Z, Y, gamma may be NULL to skip it. */
+int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_t on_device,
+                     int32_t* kr_out, int32_t* is_complex);
+int sylv_adi_destroy(sylv_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYLV_ADI_H */

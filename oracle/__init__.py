@@ -1,0 +1,30 @@
+"""CPU FP64 oracle for the inexact low-rank Sylvester ADI method.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check of the package
+and the CPU-baseline leg of the benchmark may import this package.  The CUDA
+path never calls it and shares no code with it; the two meet only through
+the seeded inputs of ``paper_2312_02891_gb300.workloads``.
+
+The oracle is written for a reader who checks it against the paper
+(Kuerschner, "Inexact linear solves in the low-rank ADI iteration for large
+Sylvester equations"): plain numpy / scipy, float64 (complex128 for complex
+shifts), no blocking or fusion.
+
+Modules
+-------
+controller  eqs. (ADI_relax1_prak), (upd_resgap), (ADI_relax2_prak),
+            (simple_tols), (one_side): the inner tolerances delta^A_k, delta^B_k.
+gmres       restarted GMRES(m) with right Jacobi preconditioning, the inner
+            solver of the shifted systems (Sec. 3.3 "Further implementation
+            aspects": per-column solves, ||r(:,l)|| <= delta_k / r).
+lradi       Algorithm 1 (inexact LR-ADI) with direct or GMRES inner solves.
+residual    exact norms through low-rank factors: ||w t^*||, the true
+            residual of eq. (adi_res_inexact), differences of factored X.
+dense       the plain definition of the solution of eq. (sylv): Kronecker
+            solve and Bartels-Stewart (scipy), for pinning on small inputs.
+
+Pins: every function is checked in tests/test_oracle_*.py against closed
+forms, dense solves, the identities of Theorems 1 and 2, and the bound of
+Theorem 3.  Functions without such a pin say "parity unpinned" in their
+docstring.
+"""

@@ -1,0 +1,149 @@
+"""Restarted GMRES(m) with right Jacobi preconditioning for shifted systems.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Solves (Op + sigma I) x = b for one column b, the inner systems of
+Algorithm 1: (A + beta_k I) z = w_{k-1}(:, l) and (B^T + conj(alpha_k) I)
+y = t_{k-1}(:, l).  The paper's guidance for the inner solver (Sec. 3.3,
+"Further implementation aspects"):
+
+* each of the r columns is solved separately, to ||r(:,l)|| <= delta_k / r;
+* right preconditioning, so the Krylov residual estimate is the residual of
+  the original system; the true residual is recomputed after termination and
+  a new cycle starts if it is not yet below the tolerance.
+
+The paper uses BiCGstab/MINRES in its experiments; restarted GMRES is the
+textbook method of Saad and Schultz (1986) with Givens rotations for the
+Hessenberg least-squares problem.  Orthogonalisation is either modified
+Gram-Schmidt or classical Gram-Schmidt applied twice (CGS2); both are
+written out plainly below.  Initial guess x0 = 0 (the paper is silent).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class GmresResult:
+    x: np.ndarray           # approximate solution
+    resnorm: float          # ||b - (Op + sigma I) x||_2, recomputed explicitly
+    iters: int              # Arnoldi steps (operator applications inside cycles)
+    cycles: int             # restart cycles run
+    converged: bool
+    history: list           # Givens residual estimates, one per Arnoldi step
+
+
+def givens(a, b):
+    """Rotation [[c, s], [-conj(s), c]] (c real) mapping (a, b) to (rho, 0)."""
+    aa, ab = abs(a), abs(b)
+    if ab == 0.0:
+        return 1.0, 0.0 * a
+    if aa == 0.0:
+        return 0.0, np.conj(b) / ab
+    rho = np.hypot(aa, ab)
+    c = aa / rho
+    s = (a / aa) * np.conj(b) / rho
+    return c, s
+
+
+def mgs_step(V, w):
+    """Modified Gram-Schmidt of w against the rows of V: (h, w - V^T h)."""
+    h = np.zeros(V.shape[0], dtype=np.result_type(V.dtype, w.dtype))
+    for i in range(V.shape[0]):
+        h[i] = np.vdot(V[i], w)
+        w = w - h[i] * V[i]
+    return h, w
+
+
+def cgs2_step(V, w):
+    """Classical Gram-Schmidt applied twice: h1 = V^* w, w1 = w - V h1,
+    h2 = V^* w1, w2 = w1 - V h2; returns (h1 + h2, w2).  V holds the
+    orthonormal vectors as rows."""
+    h1 = V.conj() @ w
+    w = w - V.T @ h1
+    h2 = V.conj() @ w
+    w = w - V.T @ h2
+    return h1 + h2, w
+
+
+def shifted_apply(S, sigma, x):
+    """(Op + sigma I) x."""
+    return S @ x + sigma * x
+
+
+def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
+          jacobi: bool = False, ortho: str = "cgs2") -> GmresResult:
+    """GMRES(restart) for (S + sigma I) x = b, stop when ||b - (S+sigma I)x|| <= tol.
+
+    S is a scipy sparse matrix, sigma a real or complex scalar.  With
+    jacobi=True the method runs on (S + sigma I) P^{-1} u = b with
+    P = diag(S) + sigma I and returns x = P^{-1} u.
+    """
+    dtype = np.result_type(S.dtype, np.asarray(sigma).dtype, b.dtype)
+    n = b.shape[0]
+    b = b.astype(dtype)
+    pinv = 1.0 / (S.diagonal().astype(dtype) + sigma) if jacobi else np.ones(n, dtype)
+    x = np.zeros(n, dtype)
+    r = b.copy()
+    beta = np.linalg.norm(r)
+    hist = []
+    iters = cycles = 0
+    if beta <= tol:
+        return GmresResult(x, beta, 0, 0, True, hist)
+    m = restart
+    while True:
+        cycles += 1
+        V = np.zeros((m + 1, n), dtype)
+        R = np.zeros((m + 1, m), dtype)     # Hessenberg columns, rotated in place
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype)
+        g = np.zeros(m + 1, dtype)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            w = shifted_apply(S, sigma, pinv * V[j])
+            iters += 1
+            h = np.zeros(j + 2, dtype)
+            if ortho == "mgs":
+                h[: j + 1], w = mgs_step(V[: j + 1], w)
+            elif ortho == "cgs2":
+                h[: j + 1], w = cgs2_step(V[: j + 1], w)
+            else:
+                raise ValueError(ortho)
+            hn = np.linalg.norm(w)
+            h[j + 1] = hn
+            if hn > 0.0:
+                V[j + 1] = w / hn
+            # apply the previous rotations to the new column
+            for i in range(j):
+                t0 = cs[i] * h[i] + sn[i] * h[i + 1]
+                t1 = -np.conj(sn[i]) * h[i] + cs[i] * h[i + 1]
+                h[i], h[i + 1] = t0, t1
+            c, s = givens(h[j], h[j + 1])
+            cs[j], sn[j] = c, s
+            h[j] = c * h[j] + s * h[j + 1]
+            h[j + 1] = 0.0
+            g[j + 1] = -np.conj(s) * g[j]
+            g[j] = c * g[j]
+            R[: j + 2, j] = h
+            est = abs(g[j + 1])
+            hist.append(est)
+            j_done = j + 1
+            if est <= tol or iters >= max_iters:
+                break
+        # least-squares solution: back substitution with the rotated R
+        k = j_done
+        y = np.zeros(k, dtype)
+        for i in range(k - 1, -1, -1):
+            acc = g[i] - R[i, i + 1: k] @ y[i + 1: k]
+            y[i] = acc / R[i, i] if R[i, i] != 0 else 0.0
+        x = x + pinv * (V[:k].T @ y)
+        r = b - shifted_apply(S, sigma, x)
+        beta = np.linalg.norm(r)
+        if beta <= tol:
+            return GmresResult(x, beta, iters, cycles, True, hist)
+        if iters >= max_iters:
+            return GmresResult(x, beta, iters, cycles, False, hist)

@@ -1,0 +1,183 @@
+"""Algorithm 1 (inexact LR-ADI for Sylvester equations), M = I, C = I.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Solves A X + X B = -f g^* (eq. (sylv)) for X ~ Z Gamma Y^*, following the
+steps of Algorithm 1 in the paper's order:
+
+  w_0 = f, t_0 = g, Z = Y = Gamma = [], k = 1
+  while ||w_{k-1} t_{k-1}^*|| >= tau ||f g^*||:
+      (delta^A_k, delta^B_k) from the controller (Sec. 3.3)
+      solve (A + beta_k I) z_k = w_{k-1}      to ||r^A_k|| <= delta^A_k
+      solve (B + alpha_k I)^* y_k = t_{k-1}   to ||r^B_k|| <= delta^B_k
+      gamma_k = -(beta_k + alpha_k)
+      w_k = w_{k-1} + gamma_k z_k,  t_k = t_{k-1} + conj(gamma_k) y_k
+      Z = [Z, z_k], Y = [Y, y_k], Gamma = diag(Gamma, gamma_k I_r)
+      u_k, v_k by eq. (upd_resgap)
+      k = k + 1
+
+Readings where the paper is silent or inconsistent:
+* The inner systems use (A + beta_k I) and (B + alpha_k I)^* as in
+  Algorithm 1 and eq. (lradi_basic) (eq. (linres) swaps the shifts).
+* Gamma's diagonal is gamma_k = -(beta_k + alpha_k) (Algorithm 1), not the
+  fADI entry beta_k - alpha_k.
+* eps = tau ||f g^*||_2: the absolute residual-gap target; delta_min,
+  delta_max and the fixed tolerance are absolute numbers.
+* Each of the r columns is solved separately to delta_k / r; ||r^A_k|| etc.
+  are spectral norms of the n x r blocks.
+* u, v use the achieved inner residual norms.
+* Shifts are reused cyclically when k exceeds their number.
+* With complex shifts, conjugate pairs (alpha_{k+1}, beta_{k+1}) =
+  (conj alpha_k, conj beta_k) are consecutive and the outer stop test is
+  skipped after the first member of a pair.
+* An inner solve that reaches its iteration cap keeps its best iterate and
+  its achieved residual feeds u, v.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import controller as ctl
+from .gmres import gmres
+from .residual import block_norm2, lowrank_norm2
+
+DEFAULTS = dict(strategy="bl_mid", inner="gmres", restart=30, max_inner=20000,
+                jacobi=False, xi=1.0, dmin_A=None, dmin_B=None, dmax_A=0.1,
+                dmax_B=0.1, kmax=50, fixed_tol=None, ortho="cgs2",
+                keep_inner_residuals=False)
+
+
+@dataclass
+class LradiResult:
+    Z: np.ndarray
+    Y: np.ndarray
+    gamma: np.ndarray           # diagonal of Gamma (length k*r)
+    steps: int                  # outer steps taken
+    converged: bool
+    res_comp: float             # ||w t^*|| / ||f g^*|| at exit
+    inner_its_A: int
+    inner_its_B: int
+    history: list = field(default_factory=list)
+    S_A: np.ndarray | None = None
+    S_B: np.ndarray | None = None
+    w: np.ndarray | None = None
+    t: np.ndarray | None = None
+
+
+def _as_scipy(M):
+    if hasattr(M, "to_scipy"):
+        return M.to_scipy()
+    return sp.csr_matrix(M)
+
+
+def _is_pair_start(alpha, beta, idx):
+    """True when shift idx opens a conjugate pair completed by idx+1."""
+    L = len(alpha)
+    a, b = alpha[idx], beta[idx]
+    if np.imag(a) == 0 and np.imag(b) == 0:
+        return False
+    if idx + 1 >= L:
+        return False
+    return np.conj(a) == alpha[idx + 1] and np.conj(b) == beta[idx + 1]
+
+
+def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, **opts) -> LradiResult:
+    o = dict(DEFAULTS)
+    unknown = set(opts) - set(o)
+    if unknown:
+        raise TypeError(f"unknown options {sorted(unknown)}")
+    o.update(opts)
+    if o["dmin_A"] is None:
+        o["dmin_A"] = tau / 20
+    if o["dmin_B"] is None:
+        o["dmin_B"] = tau / 20
+    if o["fixed_tol"] is None:
+        o["fixed_tol"] = tau / 20
+    SA = _as_scipy(A)
+    SBt = _as_scipy(B).T.tocsr()            # (B + alpha I)^* = B^T + conj(alpha) I for real B
+    alpha = np.asarray(alpha)
+    beta = np.asarray(beta)
+    cplx = np.iscomplexobj(alpha) or np.iscomplexobj(beta) or np.iscomplexobj(f)
+    dt = np.complex128 if cplx else np.float64
+    n, r = f.shape
+    m = g.shape[0]
+    w = f.astype(dt).copy()
+    t = g.astype(dt).copy()
+    nfg = lowrank_norm2(f, g)
+    if nfg == 0.0:
+        # f g^* = 0: X = 0 solves eq. (sylv) exactly, no step is taken
+        return LradiResult(np.zeros((n, 0), dt), np.zeros((m, 0), dt), np.zeros(0, dt), 0, True,
+                           0.0, 0, 0, [], None, None, w, t)
+    eps = tau * nfg
+    Zs, Ys, gammas, hist = [], [], [], []
+    SAs, SBs = [], []
+    u = v = 0.0
+    itsA_tot = itsB_tot = 0
+    lu_cache = {}
+    k = 1
+    converged = False
+    pair_open = False
+    res = lowrank_norm2(w, t)
+    while True:
+        if not pair_open and res < tau * nfg:
+            converged = True
+            break
+        if k > o["kmax"]:
+            break
+        idx = (k - 1) % len(alpha)
+        a_k, b_k = alpha[idx], beta[idx]
+        N_w, N_t = block_norm2(w), block_norm2(t)
+        dA, dB, eh = ctl.inner_tolerances(
+            o["strategy"], k=k, kmax=o["kmax"], eps=eps, xi=o["xi"], u_prev=u, v_prev=v,
+            N_w=N_w, N_t=N_t, dmin_A=o["dmin_A"], dmax_A=o["dmax_A"],
+            dmin_B=o["dmin_B"], dmax_B=o["dmax_B"], fixed_tol=o["fixed_tol"])
+        z = np.zeros((n, r), dt)
+        y = np.zeros((m, r), dt)
+        itsA = itsB = 0
+        okA = okB = True
+        for l in range(r):
+            if o["inner"] == "direct":
+                key = ("A", complex(b_k))
+                if key not in lu_cache:
+                    lu_cache[key] = spla.splu((SA + b_k * sp.eye(n)).astype(dt).tocsc())
+                z[:, l] = lu_cache[key].solve(w[:, l])
+                key = ("B", complex(a_k))
+                if key not in lu_cache:
+                    lu_cache[key] = spla.splu((SBt + np.conj(a_k) * sp.eye(m)).astype(dt).tocsc())
+                y[:, l] = lu_cache[key].solve(t[:, l])
+            else:
+                ra = gmres(SA, b_k, w[:, l], dA / r, o["restart"], o["max_inner"],
+                           o["jacobi"], o["ortho"])
+                rb = gmres(SBt, np.conj(a_k), t[:, l], dB / r, o["restart"], o["max_inner"],
+                           o["jacobi"], o["ortho"])
+                z[:, l], y[:, l] = ra.x, rb.x
+                itsA += ra.iters; itsB += rb.iters
+                okA &= ra.converged; okB &= rb.converged
+        rA = w - (SA @ z + b_k * z)
+        rB = t - (SBt @ y + np.conj(a_k) * y)
+        gam = -(b_k + a_k)
+        w = w + gam * z
+        t = t + np.conj(gam) * y
+        Zs.append(z); Ys.append(y); gammas.extend([gam] * r)
+        if o["keep_inner_residuals"]:
+            SAs.append(rA); SBs.append(rB)
+        nrA, nrB = block_norm2(rA), block_norm2(rB)
+        u = u + abs(gam) * block_norm2(z) * nrB
+        v = v + abs(gam) * block_norm2(y) * nrA
+        itsA_tot += itsA; itsB_tot += itsB
+        res = lowrank_norm2(w, t)
+        hist.append(dict(k=k, alpha=a_k, beta=b_k, dA=dA, dB=dB, eps_hat=eh, nrA=nrA, nrB=nrB,
+                         itsA=itsA, itsB=itsB, okA=okA, okB=okB, u=u, v=v,
+                         res_comp=res / nfg, N_w=N_w, N_t=N_t))
+        pair_open = _is_pair_start(alpha, beta, idx) and not pair_open
+        k += 1
+    Z = np.hstack(Zs) if Zs else np.zeros((n, 0), dt)
+    Y = np.hstack(Ys) if Ys else np.zeros((m, 0), dt)
+    return LradiResult(Z, Y, np.array(gammas, dtype=dt), k - 1, converged, res / nfg,
+                       itsA_tot, itsB_tot, hist,
+                       np.hstack(SAs) if SAs else None, np.hstack(SBs) if SBs else None,
+                       w, t)

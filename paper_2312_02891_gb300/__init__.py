@@ -1,0 +1,352 @@
+"""GB300 inexact low-rank Sylvester ADI: Python binding of libsylv_adi.so.
+
+The functions below carry the names of the C ABI in include/sylv_adi.h and
+only marshal arguments (numpy arrays for host data, integer device pointers
+or objects with ``data_ptr()`` such as torch CUDA tensors for device data).
+Every step of the computation runs in the CUDA library; if the library is
+missing the calls raise instead of computing anything on the CPU.
+
+``SylvesterADI`` wraps a solver handle for numpy inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+__all__ = [
+    "SylvError", "lib_path", "load", "SylvOpts", "SylvInfo", "SylvShift", "SylvCsr",
+    "STRATEGIES", "sylv_opts_default", "sylv_last_error", "sylv_op_create", "sylv_op_format",
+    "sylv_op_apply", "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval",
+    "sylv_adi_create", "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve",
+    "sylv_adi_info", "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "SylvesterADI",
+    "HIST_COLUMNS", "EXPORTED",
+]
+
+SYLV_OK = 0
+ERRORS = {-1: "INVALID", -2: "CUDA", -3: "NOMEM", -4: "MAXIT", -5: "INNER_STALL",
+          -6: "NONFINITE", -7: "NOT_SOLVED", -8: "UNSUPPORTED"}
+WARNINGS = (-4, -5)      # solve finished, factors valid
+STRATEGIES = {"fixed": 0, "nobl_mid": 1, "bl_mid": 2, "nobl_A": 3, "bl_A": 4, "nobl_B": 5, "bl_B": 6}
+HIST_COLUMNS = ("k", "alpha", "beta", "dA", "dB", "eps_hat", "nrA", "nrB", "itsA", "itsB",
+                "u", "v", "res_comp", "N_w")
+EXPORTED = (
+    "sylv_last_error", "sylv_opts_default", "sylv_op_create", "sylv_op_format", "sylv_op_apply",
+    "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval", "sylv_adi_create",
+    "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
+    "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy",
+)
+
+
+class SylvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SylvCsr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p),
+                ("on_device", C.c_int32)]
+
+
+class SylvShift(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class SylvOpts(C.Structure):
+    _fields_ = [("xi", C.c_double), ("dmin_A", C.c_double), ("dmin_B", C.c_double),
+                ("dmax_A", C.c_double), ("dmax_B", C.c_double), ("kmax", C.c_int32),
+                ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
+                ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
+                ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32)]
+
+
+class SylvInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps", C.c_int32), ("kr", C.c_int32),
+                ("is_complex", C.c_int32), ("rel_res_comp", C.c_double), ("norm_fg", C.c_double),
+                ("inner_its_A", C.c_int64), ("inner_its_B", C.c_int64),
+                ("inner_restarts", C.c_int64), ("stalled_solves", C.c_int32),
+                ("ticks", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def lib_path() -> Path:
+    return Path(__file__).resolve().parent / "_lib" / "libsylv_adi.so"
+
+
+def load():
+    """Load libsylv_adi.so (built by _build.build()); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = lib_path()
+    if not p.exists():
+        raise RuntimeError(f"{p} is not built: run paper_2312_02891_gb300._build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = C.CDLL(str(p))
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    pd, pi32 = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "sylv_last_error": ([], C.c_char_p),
+        "sylv_opts_default": ([C.POINTER(SylvOpts)], C.c_int),
+        "sylv_op_create": ([C.POINTER(SylvCsr), i32, C.POINTER(vp)], C.c_int),
+        "sylv_op_format": ([vp, pi32, pi32, pi32], C.c_int),
+        "sylv_op_apply": ([vp, SylvShift, i32, i32, vp, vp, i32, vp], C.c_int),
+        "sylv_op_destroy": ([vp], C.c_int),
+        "sylv_cgs2": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
+        "sylv_gmres": ([vp, SylvShift, i32, i32, vp, vp, i32, d, i32, i32, pi32, pd, pd, vp], C.c_int),
+        "sylv_controller_eval": ([C.POINTER(SylvOpts), i32, pd, pd], C.c_int),
+        "sylv_adi_create": ([C.POINTER(SylvCsr), C.POINTER(SylvCsr), pd, pd, i32,
+                             C.POINTER(SylvShift), C.POINTER(SylvShift), i32, d,
+                             C.POINTER(SylvOpts), vp, C.POINTER(vp)], C.c_int),
+        "sylv_adi_set_rhs": ([vp, pd, pd], C.c_int),
+        "sylv_adi_set_rhs_device": ([vp, vp, vp], C.c_int),
+        "sylv_adi_solve": ([vp], C.c_int),
+        "sylv_adi_info": ([vp, C.POINTER(SylvInfo)], C.c_int),
+        "sylv_adi_history": ([vp, pd, i32, pi32], C.c_int),
+        "sylv_adi_factors": ([vp, vp, vp, vp, i32, pi32, pi32], C.c_int),
+        "sylv_adi_destroy": ([vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+def sylv_last_error() -> str:
+    return load().sylv_last_error().decode()
+
+
+def _check(rc: int, allow_warn: bool = False) -> int:
+    if rc == SYLV_OK or (allow_warn and rc in WARNINGS):
+        return rc
+    raise SylvError(rc, sylv_last_error())
+
+
+def _ptr(x) -> int | None:
+    """Device or host address of x (int, torch tensor, numpy array) or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return getattr(s, "cuda_stream", None)
+
+
+def _shift(s) -> SylvShift:
+    s = complex(s)
+    return SylvShift(s.real, s.imag)
+
+
+def sylv_opts_default(**overrides) -> SylvOpts:
+    o = SylvOpts()
+    _check(load().sylv_opts_default(C.byref(o)))
+    for k, v in overrides.items():
+        if k == "strategy" and isinstance(v, str):
+            v = STRATEGIES[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class _HostCsr:
+    """Keeps the contiguous host arrays of a CSR alive while C reads them."""
+
+    def __init__(self, n, rowptr, colind, val):
+        self.rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self.ci = np.ascontiguousarray(colind, dtype=np.int32)
+        self.v = np.ascontiguousarray(val, dtype=np.float64)
+        self.s = SylvCsr(n, n, int(self.rp[-1]), self.rp.ctypes.data, self.ci.ctypes.data,
+                         self.v.ctypes.data, 0)
+
+
+def _csr(M) -> _HostCsr:
+    if hasattr(M, "rowptr"):
+        return _HostCsr(M.n, M.rowptr, M.colind, M.val)
+    return _HostCsr(M.shape[0], M.indptr, M.indices, M.data)   # scipy.sparse.csr_matrix
+
+
+def sylv_op_create(M, transpose: bool = False) -> int:
+    h = _csr(M)
+    out = C.c_void_p()
+    _check(load().sylv_op_create(C.byref(h.s), int(transpose), C.byref(out)))
+    return out.value
+
+
+def sylv_op_format(op) -> tuple[int, int, int]:
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().sylv_op_format(op, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sylv_op_apply(op, sigma, jacobi, is_complex, X, Y, ncols, stream=None) -> None:
+    _check(load().sylv_op_apply(op, _shift(sigma), int(jacobi), int(is_complex), _ptr(X), _ptr(Y),
+                                int(ncols), _stream(stream)))
+
+
+def sylv_op_destroy(op) -> None:
+    _check(load().sylv_op_destroy(op))
+
+
+def sylv_cgs2(V, n, k, w, is_complex=False, stream=None) -> np.ndarray:
+    """CGS2 of device vector w against k device columns V; returns h (k+1)."""
+    h = np.zeros(2 * (k + 1) if is_complex else k + 1)
+    _check(load().sylv_cgs2(_ptr(V), int(n), int(k), _ptr(w), h.ctypes.data, int(is_complex),
+                            _stream(stream)))
+    return h.view(np.complex128) if is_complex else h
+
+
+def sylv_gmres(op, sigma, jacobi, is_complex, B, X, ncols, tol, restart, max_iters,
+               want_hist=False, stream=None):
+    """Returns (status, iters[ncols], resnorm[ncols], hist or None)."""
+    iters = np.zeros(ncols, dtype=np.int32)
+    res = np.zeros(ncols)
+    hist = np.zeros((ncols, max_iters)) if want_hist else None
+    rc = load().sylv_gmres(op, _shift(sigma), int(jacobi), int(is_complex), _ptr(B), _ptr(X),
+                           int(ncols), float(tol), int(restart), int(max_iters),
+                           iters.ctypes.data_as(C.POINTER(C.c_int32)),
+                           res.ctypes.data_as(C.POINTER(C.c_double)),
+                           hist.ctypes.data_as(C.POINTER(C.c_double)) if want_hist else None,
+                           _stream(stream))
+    _check(rc, allow_warn=True)
+    return rc, iters, res, hist
+
+
+def sylv_controller_eval(opts: SylvOpts, inputs: np.ndarray) -> np.ndarray:
+    inp = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, 11)
+    out = np.zeros((inp.shape[0], 3))
+    _check(load().sylv_controller_eval(C.byref(opts), inp.shape[0],
+                                       inp.ctypes.data_as(C.POINTER(C.c_double)),
+                                       out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def sylv_adi_create(A, B, f, g, alpha, beta, tau, opts: SylvOpts | None = None, stream=None) -> int:
+    ha, hb = _csr(A), _csr(B)
+    f = np.asfortranarray(f, dtype=np.float64)
+    g = np.asfortranarray(g, dtype=np.float64)
+    r = f.shape[1]
+    if g.shape[1] != r:
+        raise ValueError("f and g need the same number of columns")
+    al = (SylvShift * len(alpha))(*[_shift(a) for a in alpha])
+    be = (SylvShift * len(beta))(*[_shift(b) for b in beta])
+    if len(alpha) != len(beta):
+        raise ValueError("alpha and beta need the same length")
+    out = C.c_void_p()
+    _check(load().sylv_adi_create(C.byref(ha.s), C.byref(hb.s),
+                                  f.ctypes.data_as(C.POINTER(C.c_double)),
+                                  g.ctypes.data_as(C.POINTER(C.c_double)), r, al, be, len(alpha),
+                                  float(tau), C.byref(opts) if opts is not None else None,
+                                  _stream(stream), C.byref(out)))
+    return out.value
+
+
+def sylv_adi_set_rhs(h, f, g) -> None:
+    f = np.asfortranarray(f, dtype=np.float64)
+    g = np.asfortranarray(g, dtype=np.float64)
+    _check(load().sylv_adi_set_rhs(h, f.ctypes.data_as(C.POINTER(C.c_double)),
+                                   g.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def sylv_adi_set_rhs_device(h, f, g) -> None:
+    _check(load().sylv_adi_set_rhs_device(h, _ptr(f), _ptr(g)))
+
+
+def sylv_adi_solve(h) -> int:
+    """Runs Algorithm 1; returns the status (0, or MAXIT/INNER_STALL warnings)."""
+    return _check(load().sylv_adi_solve(h), allow_warn=True)
+
+
+def sylv_adi_info(h) -> dict:
+    info = SylvInfo()
+    _check(load().sylv_adi_info(h, C.byref(info)))
+    return info.as_dict()
+
+
+def sylv_adi_history(h, cap: int = 1000) -> np.ndarray:
+    buf = np.zeros((cap, len(HIST_COLUMNS)))
+    rows = C.c_int32()
+    _check(load().sylv_adi_history(h, buf.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(rows)))
+    return buf[: rows.value]
+
+
+def sylv_adi_factors(h, n: int, m: int):
+    """(Z, Y, gamma) as numpy arrays (host copies)."""
+    info = sylv_adi_info(h)
+    kr, cplx = info["kr"], info["is_complex"]
+    dt = np.complex128 if cplx else np.float64
+    Z = np.zeros((kr, n), dtype=dt)        # column-major n x kr == row-major kr x n
+    Y = np.zeros((kr, m), dtype=dt)
+    gam = np.zeros(kr, dtype=dt)
+    kro, isc = C.c_int32(), C.c_int32()
+    _check(load().sylv_adi_factors(h, Z.ctypes.data, Y.ctypes.data, gam.ctypes.data, 0,
+                                   C.byref(kro), C.byref(isc)))
+    return Z.T, Y.T, gam
+
+
+def sylv_adi_destroy(h) -> None:
+    _check(load().sylv_adi_destroy(h))
+
+
+class SylvesterADI:
+    """A X + X B = -f g^* solved on the GPU by the inexact LR-ADI iteration."""
+
+    def __init__(self, A, B, f, g, alpha, beta, tau=1e-8, stream=None, **opts):
+        self.n = A.n if hasattr(A, "n") else A.shape[0]
+        self.m = B.n if hasattr(B, "n") else B.shape[0]
+        self.r = f.shape[1]
+        self.opts = sylv_opts_default(**opts)
+        self.h = sylv_adi_create(A, B, f, g, alpha, beta, tau, self.opts, stream)
+
+    def solve(self) -> int:
+        return sylv_adi_solve(self.h)
+
+    def set_rhs(self, f, g) -> None:
+        sylv_adi_set_rhs(self.h, f, g)
+
+    def info(self) -> dict:
+        return sylv_adi_info(self.h)
+
+    def history(self) -> np.ndarray:
+        return sylv_adi_history(self.h)
+
+    def factors(self):
+        return sylv_adi_factors(self.h, self.n, self.m)
+
+    def close(self) -> None:
+        if self.h:
+            sylv_adi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,219 @@
+// api.cu - the extern "C" boundary declared in include/sylv_adi.h.  Argument
+// checking and dispatch only; every step of the solve runs in the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include "internal.h"
+
+namespace sylv {
+const char* last_error_cstr();
+}
+
+using namespace sylv;
+
+static bool shift_is_complex(sylv_shift s) { return s.im != 0.0; }
+
+extern "C" {
+
+const char* sylv_last_error(void) { return last_error_cstr(); }
+
+int sylv_opts_default(sylv_opts* o) {
+    if (!o) { set_error("sylv_opts_default: null"); return SYLV_ERR_INVALID; }
+    std::memset(o, 0, sizeof(*o));
+    o->xi = 1.0;
+    o->dmin_A = o->dmin_B = 0.0;        // tau / 20 at create
+    o->dmax_A = o->dmax_B = 0.1;
+    o->kmax = 50;
+    o->strategy = SYLV_STRAT_BL_MID;
+    o->fixed_tol = 0.0;                 // tau / 20 at create
+    o->restart = 30;
+    o->max_inner = 20000;
+    o->precision = SYLV_PREC_FP64;
+    o->jacobi = 1;
+    o->bl_clamp = 0;
+    o->rows_per_chunk = 0;
+    return SYLV_OK;
+}
+
+int sylv_op_create(const sylv_csr* csr, int32_t transpose, sylv_op** out) {
+    if (!out) { set_error("sylv_op_create: null out"); return SYLV_ERR_INVALID; }
+    *out = nullptr;
+    HostCsr h, ht;
+    SYLV_TRY(load_csr(csr, h));
+    sylv_op* op = new (std::nothrow) sylv_op();
+    if (!op) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
+    int rc;
+    if (transpose) { transpose_csr(h, ht); rc = op->op.upload(ht); }
+    else rc = op->op.upload(h);
+    if (rc != SYLV_OK) { op->op.release(); delete op; return rc; }
+    *out = op;
+    return SYLV_OK;
+}
+
+int sylv_op_format(const sylv_op* op, int32_t* is_stencil, int32_t* ndiag, int32_t* n) {
+    if (!op) { set_error("sylv_op_format: null op"); return SYLV_ERR_INVALID; }
+    if (is_stencil) *is_stencil = op->op.is_stencil;
+    if (ndiag) *ndiag = op->op.desc.ndiag;
+    if (n) *n = op->op.desc.n;
+    return SYLV_OK;
+}
+
+int sylv_op_apply(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+                  const void* X, void* Y, int32_t ncols, void* stream) {
+    if (!op) { set_error("sylv_op_apply: null op"); return SYLV_ERR_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (is_complex) return op_apply_cplx(op->op, sigma, jacobi, X, Y, ncols, s);
+    if (shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
+    return op_apply_real(op->op, sigma.re, jacobi, X, Y, ncols, s);
+}
+
+int sylv_op_destroy(sylv_op* op) {
+    if (!op) return SYLV_OK;
+    op->op.release();
+    delete op;
+    return SYLV_OK;
+}
+
+int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out, int32_t is_complex, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    return is_complex ? cgs2_cplx(V, n, k, w, h_out, s) : cgs2_real(V, n, k, w, h_out, s);
+}
+
+int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+               const void* B, void* X, int32_t ncols, double tol, int32_t restart,
+               int32_t max_iters, int32_t* iters_out, double* resnorm_out, double* hist_out,
+               void* stream) {
+    if (!op) { set_error("sylv_gmres: null op"); return SYLV_ERR_INVALID; }
+    if (!(tol >= 0.0)) { set_error("sylv_gmres: tol must be >= 0"); return SYLV_ERR_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (is_complex)
+        return gmres_cplx(op->op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters_out,
+                          resnorm_out, hist_out, s);
+    if (shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
+    return gmres_real(op->op, sigma.re, jacobi, B, X, ncols, tol, restart, max_iters, iters_out,
+                      resnorm_out, hist_out, s);
+}
+
+int sylv_controller_eval(const sylv_opts* o, int32_t count, const double* in, double* out) {
+    return controller_eval_dev(o, count, in, out);
+}
+
+int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const double* g,
+                    int32_t r, const sylv_shift* alpha, const sylv_shift* beta, int32_t n_shifts,
+                    double tol, const sylv_opts* opts, void* stream, sylv_handle** out) {
+    if (!out) { set_error("sylv_adi_create: null out"); return SYLV_ERR_INVALID; }
+    *out = nullptr;
+    if (!f || !g || !alpha || !beta || n_shifts <= 0) {
+        set_error("sylv_adi_create: null f/g/shifts or n_shifts <= 0");
+        return SYLV_ERR_INVALID;
+    }
+    if (r < 1 || r > SYLV_MAX_RANK) {
+        set_error("rank r=%d outside 1..%d", r, SYLV_MAX_RANK);
+        return r < 1 ? SYLV_ERR_INVALID : SYLV_ERR_UNSUPPORTED;
+    }
+    if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must lie in (0, 1)"); return SYLV_ERR_INVALID; }
+    sylv_opts o;
+    if (opts) o = *opts; else sylv_opts_default(&o);
+    if (o.dmin_A <= 0) o.dmin_A = tol / 20;
+    if (o.dmin_B <= 0) o.dmin_B = tol / 20;
+    if (o.fixed_tol <= 0) o.fixed_tol = tol / 20;
+    if (o.restart < 1 || o.restart > SYLV_MAX_RESTART) {
+        set_error("restart %d outside 1..%d", o.restart, SYLV_MAX_RESTART);
+        return SYLV_ERR_UNSUPPORTED;
+    }
+    if (o.kmax < 1 || o.max_inner < 1 || o.strategy < 0 || o.strategy > SYLV_STRAT_BL_B ||
+        !(o.xi > 0.0 && o.xi <= 1.0) || !(o.dmax_A > 0) || !(o.dmax_B > 0)) {
+        set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
+        return SYLV_ERR_INVALID;
+    }
+    if (o.precision != SYLV_PREC_FP64) { set_error("precision %d not built", o.precision); return SYLV_ERR_UNSUPPORTED; }
+    bool cplx = false;
+    for (int i = 0; i < n_shifts; ++i) {
+        if (!std::isfinite(alpha[i].re) || !std::isfinite(alpha[i].im) || !std::isfinite(beta[i].re) ||
+            !std::isfinite(beta[i].im)) {
+            set_error("non-finite shift %d", i);
+            return SYLV_ERR_INVALID;
+        }
+        cplx |= shift_is_complex(alpha[i]) || shift_is_complex(beta[i]);
+    }
+    if (cplx) {
+        // conjugate pairs must be adjacent: a complex pair at i is followed by its conjugate
+        for (int i = 0; i < n_shifts; ++i) {
+            if (!(shift_is_complex(alpha[i]) || shift_is_complex(beta[i]))) continue;
+            if (i + 1 >= n_shifts || alpha[i + 1].re != alpha[i].re || alpha[i + 1].im != -alpha[i].im ||
+                beta[i + 1].re != beta[i].re || beta[i + 1].im != -beta[i].im) {
+                set_error("complex shift pair %d is not followed by its conjugate pair", i);
+                return SYLV_ERR_INVALID;
+            }
+            ++i;
+        }
+    }
+    sylv_handle* h = new (std::nothrow) sylv_handle();
+    if (!h) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
+    h->stream = (cudaStream_t)stream;
+    h->is_complex = cplx ? 1 : 0;
+    HostCsr ha, hb, hbt;
+    int rc = load_csr(A, ha);
+    if (rc == SYLV_OK) rc = load_csr(B, hb);
+    if (rc == SYLV_OK) { transpose_csr(hb, hbt); rc = h->A.upload(ha); }
+    if (rc == SYLV_OK) rc = h->Bt.upload(hbt);
+    if (rc == SYLV_OK) {
+        AdiArgs a{&h->A, &h->Bt, ha.n, hb.n, r, f, g, alpha, beta, n_shifts, tol, o, h->stream};
+        rc = cplx ? make_adi_cplx(a, &h->impl) : make_adi_real(a, &h->impl);
+    }
+    if (rc != SYLV_OK) {
+        h->A.release();
+        h->Bt.release();
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SYLV_OK;
+}
+
+int sylv_adi_set_rhs(sylv_handle* h, const double* f, const double* g) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    return h->impl->set_rhs(f, g, 0);
+}
+
+int sylv_adi_set_rhs_device(sylv_handle* h, const double* f, const double* g) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    return h->impl->set_rhs(f, g, 1);
+}
+
+int sylv_adi_solve(sylv_handle* h) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    h->last_status = h->impl->solve();
+    h->solved = 1;
+    return h->last_status;
+}
+
+int sylv_adi_info(const sylv_handle* h, sylv_info* info) {
+    if (!h || !info) { set_error("null handle or info"); return SYLV_ERR_INVALID; }
+    return h->impl->info(info);
+}
+
+int sylv_adi_history(const sylv_handle* h, double* buf, int32_t cap, int32_t* rows) {
+    if (!h || (!buf && cap > 0)) { set_error("null handle or buffer"); return SYLV_ERR_INVALID; }
+    if (!h->solved) { set_error("no solve yet"); return SYLV_ERR_NOT_SOLVED; }
+    return h->impl->history(buf, cap, rows);
+}
+
+int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_t on_device,
+                     int32_t* kr_out, int32_t* is_complex) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    if (!h->solved) { set_error("no solve yet"); return SYLV_ERR_NOT_SOLVED; }
+    if (is_complex) *is_complex = h->is_complex;
+    return h->impl->factors(Z, Y, gamma, on_device, kr_out);
+}
+
+int sylv_adi_destroy(sylv_handle* h) {
+    if (!h) return SYLV_OK;
+    delete h->impl;
+    h->A.release();
+    h->Bt.release();
+    delete h;
+    return SYLV_OK;
+}
+
+}  // extern "C"

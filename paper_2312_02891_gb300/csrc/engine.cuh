@@ -1,0 +1,471 @@
+// engine.cuh - host orchestration of the batched GMRES solves and of the
+// inexact LR-ADI outer loop (Algorithm 1).  Instantiated for double (real
+// shifts) in inst_real.cu and for cplx (complex shifts) in inst_cplx.cu.
+#pragma once
+#include <algorithm>
+#include <cstring>
+#include <vector>
+#include "internal.h"
+#include "adi_kernels.cuh"
+
+namespace sylv {
+
+template <typename T> struct Dev;   // RAII device buffer
+template <typename T> struct Dev {
+    T* p = nullptr;
+    size_t count = 0;
+    int alloc(size_t n) {
+        release();
+        if (n == 0) return SYLV_OK;
+        cudaError_t e = cudaMalloc((void**)&p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+            return SYLV_ERR_NOMEM;
+        }
+        count = n;
+        return SYLV_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        count = 0;
+    }
+    ~Dev() { release(); }
+};
+
+inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
+
+// A batch of shifted systems solved together by restarted GMRES.
+template <typename T>
+struct Engine {
+    cudaStream_t stream = nullptr;
+    int nsys = 0, nitems = 0, restart = 30;
+    std::vector<SysDesc<T>> h_sd;
+    Dev<SysDesc<T>> d_sd;
+    Dev<SysState<T>> d_st;
+    Dev<Item> d_items;
+    Dev<OpDesc> d_ops;
+    Dev<BatchCtl> d_ctl;
+    Dev<T> d_V, d_w, d_part;
+    int* h_flag = nullptr;        // mapped pinned word
+    int* d_hflag = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long ticks = 0;
+
+    ~Engine() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (h_flag) cudaFreeHost(h_flag);
+    }
+
+    // sys_n[q], sys_op[q]: rows and operator of system q; pinv[q]: Jacobi
+    // buffer or null; hist[q]: per-step estimate buffer or null.
+    int setup(const std::vector<int>& sys_n, const std::vector<int>& sys_op,
+              const std::vector<OpDesc>& ops, const std::vector<T*>& pinv,
+              const std::vector<double*>& hist, int hist_cap, int restart_, int rpc,
+              cudaStream_t s) {
+        stream = s;
+        restart = restart_;
+        nsys = (int)sys_n.size();
+        long long total_rows = 0;
+        for (int q = 0; q < nsys; ++q) total_rows += sys_n[q];
+        if (rpc <= 0) rpc = auto_rows_per_chunk(total_rows);
+        size_t vtot = 0, wtot = 0, ptot = 0;
+        std::vector<Item> items;
+        h_sd.resize(nsys);
+        for (int q = 0; q < nsys; ++q) {
+            SysDesc<T>& d = h_sd[q];
+            d.n = sys_n[q];
+            d.op = sys_op[q];
+            d.rows_per_chunk = rpc;
+            d.nchunks = (sys_n[q] + rpc - 1) / rpc;
+            d.ldv = round_ld(sys_n[q]);
+            d.restart = restart;
+            d.hist = hist.empty() ? nullptr : hist[q];
+            d.hist_cap = hist_cap;
+            d.pinv = pinv[q];
+            vtot += (size_t)(restart + 1) * d.ldv;
+            wtot += d.ldv;
+            ptot += (size_t)d.nchunks * PSTRIDE;
+            for (int c = 0; c < d.nchunks; ++c) items.push_back({q, c});
+        }
+        nitems = (int)items.size();
+        SYLV_TRY(d_V.alloc(vtot));
+        SYLV_TRY(d_w.alloc(wtot));
+        SYLV_TRY(d_part.alloc(ptot));
+        size_t vo = 0, wo = 0, po = 0;
+        for (int q = 0; q < nsys; ++q) {
+            SysDesc<T>& d = h_sd[q];
+            d.V = d_V.p + vo;
+            d.w = d_w.p + wo;
+            d.part = d_part.p + po;
+            vo += (size_t)(restart + 1) * d.ldv;
+            wo += d.ldv;
+            po += (size_t)d.nchunks * PSTRIDE;
+        }
+        SYLV_TRY(d_sd.alloc(nsys));
+        SYLV_TRY(d_st.alloc(nsys));
+        SYLV_TRY(d_items.alloc(items.size()));
+        SYLV_TRY(d_ops.alloc(ops.size()));
+        SYLV_TRY(d_ctl.alloc(1));
+        SYLV_CK(cudaMemcpy(d_sd.p, h_sd.data(), nsys * sizeof(SysDesc<T>), cudaMemcpyHostToDevice));
+        SYLV_CK(cudaMemcpy(d_items.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
+        SYLV_CK(cudaMemcpy(d_ops.p, ops.data(), ops.size() * sizeof(OpDesc), cudaMemcpyHostToDevice));
+        SYLV_CK(cudaMemset(d_st.p, 0, nsys * sizeof(SysState<T>)));
+        SYLV_CK(cudaMemset(d_V.p, 0, vtot * sizeof(T)));
+        SYLV_CK(cudaHostAlloc((void**)&h_flag, sizeof(int), cudaHostAllocMapped));
+        *h_flag = 0;
+        SYLV_CK(cudaHostGetDevicePointer((void**)&d_hflag, h_flag, 0));
+        BatchCtl c{0, 0, d_hflag};
+        SYLV_CK(cudaMemcpy(d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
+        for (auto& e : ev) SYLV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return SYLV_OK;
+    }
+
+    // One device iteration: every active system advances one Arnoldi step
+    // and restarts if its cycle ended.
+    int launch_tick(int cgs_mode = 0) {
+        const dim3 grid(nitems), block(SYLV_BLOCK);
+        k_arnoldi_spmv<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, cgs_mode);
+        k_cgs_pass2<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p);
+        k_cgs_pass3<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
+        if (cgs_mode == 0) {
+            k_restart_update<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p);
+            k_restart_residual<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+        }
+        SYLV_CK(cudaGetLastError());
+        return SYLV_OK;
+    }
+
+    // Launch ticks until every system is done (the device clears *h_flag),
+    // keeping at most four ticks in flight.  The caller sets *h_flag = 1
+    // before the work that activates the systems.
+    int run(long long max_ticks) {
+        const int D = 4;
+        long long t = 0;
+        while (*(volatile int*)h_flag != 0) {
+            if (t >= max_ticks) {
+                set_error("inner solves did not finish within %lld device iterations", max_ticks);
+                return SYLV_ERR_INNER_STALL;
+            }
+            SYLV_TRY(launch_tick());
+            SYLV_CK(cudaEventRecord(ev[t % D], stream));
+            ++t;
+            if (t >= D) SYLV_CK(cudaEventSynchronize(ev[t % D]));
+        }
+        ticks += t;
+        return SYLV_OK;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Standalone entry points for one operator: batched GMRES, CGS2, product.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_op_apply(OpDesc op, T sigma, int jacobi, const T* __restrict__ X, T* __restrict__ Y,
+                           int ncols) {
+    const long long total = (long long)op.n * ncols;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / op.n), i = (int)(idx % op.n);
+        const T* x = X + (size_t)c * op.n;
+        T y;
+        if (jacobi)
+            y = op_row<T>(op, i, sigma, [&](int k) {
+                return sdiv(make_scalar<T>(1.0, 0.0), op.diag[k] + sigma) * x[k];
+            });
+        else
+            y = op_row<T>(op, i, sigma, [&](int k) { return x[k]; });
+        Y[(size_t)c * op.n + i] = y;
+    }
+}
+
+template <typename T>
+int op_apply_t(const DevOp& op, T sigma, int jacobi, const void* X, void* Y, int ncols, cudaStream_t s) {
+    if (!X || !Y || ncols < 0) { set_error("op_apply: null buffer or negative ncols"); return SYLV_ERR_INVALID; }
+    if (ncols == 0 || op.desc.n == 0) return SYLV_OK;
+    long long total = (long long)op.desc.n * ncols;
+    int grid = (int)std::min<long long>((total + 255) / 256, (long long)num_sms() * 16);
+    k_op_apply<T><<<grid, 256, 0, s>>>(op.desc, sigma, jacobi, (const T*)X, (T*)Y, ncols);
+    SYLV_CK(cudaGetLastError());
+    return SYLV_OK;
+}
+
+template <typename T>
+__global__ void k_copy_scaled(const T* __restrict__ src, double scale, T* __restrict__ dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = scale * src[i];
+}
+
+template <typename T>
+int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
+            int restart, int max_iters, int* iters, double* res, double* hist, cudaStream_t s) {
+    if (!B || !X || ncols <= 0 || restart < 1 || restart > SYLV_MR || max_iters < 1) {
+        set_error("gmres: invalid arguments (ncols=%d restart=%d max_iters=%d)", ncols, restart, max_iters);
+        return SYLV_ERR_INVALID;
+    }
+    const int n = op.desc.n;
+    Engine<T> eng;
+    Dev<T> pinv;
+    Dev<double> d_hist;
+    if (jacobi) SYLV_TRY(pinv.alloc(n));
+    if (hist) SYLV_TRY(d_hist.alloc((size_t)ncols * max_iters));
+    std::vector<int> sn(ncols, n), so(ncols, 0);
+    std::vector<T*> pv(ncols, jacobi ? pinv.p : nullptr);
+    std::vector<double*> hv;
+    if (hist)
+        for (int c = 0; c < ncols; ++c) hv.push_back(d_hist.p + (size_t)c * max_iters);
+    std::vector<OpDesc> ops{op.desc};
+    SYLV_TRY(eng.setup(sn, so, ops, pv, hv, max_iters, restart, 0, s));
+    std::vector<SysState<T>> st(ncols);
+    for (int c = 0; c < ncols; ++c) {
+        std::memset(&st[c], 0, sizeof(SysState<T>));
+        st[c].phase = PH_RESID;
+        st[c].max_iters = max_iters;
+        st[c].tol = tol;
+        st[c].sigma = sigma;
+        st[c].x = (T*)X + (size_t)c * n;
+        st[c].b = (const T*)B + (size_t)c * n;
+    }
+    SYLV_CK(cudaMemcpyAsync(eng.d_st.p, st.data(), ncols * sizeof(SysState<T>), cudaMemcpyHostToDevice, s));
+    BatchCtl c{ncols, 0, eng.d_hflag};
+    SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+    if (jacobi) {
+        k_pinv<T><<<num_sms() * 4, 256, 0, s>>>(op.desc.diag, sigma, pinv.p, n);
+        SYLV_CK(cudaGetLastError());
+    }
+    k_zero_x<T><<<eng.nitems, SYLV_BLOCK, 0, s>>>(eng.d_sd.p, eng.d_st.p, eng.d_items.p);
+    SYLV_CK(cudaGetLastError());
+    SYLV_CK(cudaStreamSynchronize(s));
+    *eng.h_flag = 1;
+    SYLV_TRY(eng.run((long long)max_iters + 8));
+    SYLV_CK(cudaStreamSynchronize(s));
+    SYLV_CK(cudaMemcpy(st.data(), eng.d_st.p, ncols * sizeof(SysState<T>), cudaMemcpyDeviceToHost));
+    int stalled = 0;
+    for (int c = 0; c < ncols; ++c) {
+        if (iters) iters[c] = st[c].iters;
+        if (res) res[c] = st[c].resnorm;
+        stalled |= (st[c].status != ST_OK);
+    }
+    if (hist) {
+        std::vector<double> hh((size_t)ncols * max_iters);
+        SYLV_CK(cudaMemcpy(hh.data(), d_hist.p, hh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int c = 0; c < ncols; ++c)
+            for (int i = 0; i < max_iters; ++i)
+                hist[(size_t)c * max_iters + i] = i < st[c].iters ? hh[(size_t)c * max_iters + i] : 0.0;
+    }
+    for (int c = 0; c < ncols; ++c)
+        if (st[c].status == ST_NONFINITE) { set_error("gmres: non-finite value in column %d", c); return SYLV_ERR_NONFINITE; }
+    if (stalled) { set_error("gmres: a column reached max_iters"); return SYLV_ERR_INNER_STALL; }
+    return SYLV_OK;
+}
+
+template <typename T>
+int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
+    if (!V || !w || !h || n <= 0 || k < 1 || k > SYLV_MR) {
+        set_error("cgs2: invalid arguments (n=%d k=%d, 1 <= k <= %d)", n, k, SYLV_MR);
+        return SYLV_ERR_INVALID;
+    }
+    Engine<T> eng;
+    DevOp dummy;
+    dummy.desc.n = n;
+    std::vector<OpDesc> ops{dummy.desc};
+    SYLV_TRY(eng.setup({n}, {0}, ops, {nullptr}, {}, 0, k, 0, s));
+    const SysDesc<T>& d = eng.h_sd[0];
+    for (int l = 0; l < k; ++l)
+        SYLV_CK(cudaMemcpyAsync(d.V + (size_t)l * d.ldv, (const T*)V + (size_t)l * n, n * sizeof(T),
+                                cudaMemcpyDeviceToDevice, s));
+    SYLV_CK(cudaMemcpyAsync(d.w, w, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SysState<T> st;
+    std::memset(&st, 0, sizeof(st));
+    st.phase = PH_ARNOLDI;
+    st.j = k - 1;
+    for (int l = 0; l < k; ++l) st.scale[l] = 1.0;
+    SYLV_CK(cudaMemcpyAsync(eng.d_st.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    BatchCtl c{1, 0, eng.d_hflag};
+    SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+    SYLV_TRY(eng.launch_tick(1));
+    SYLV_CK(cudaStreamSynchronize(s));
+    SYLV_CK(cudaMemcpy(&st, eng.d_st.p, sizeof(st), cudaMemcpyDeviceToHost));
+    k_copy_scaled<T><<<num_sms() * 4, 256, 0, s>>>(d.V + (size_t)k * d.ldv, st.scale[k], (T*)w, n);
+    SYLV_CK(cudaGetLastError());
+    SYLV_CK(cudaStreamSynchronize(s));
+    T* ho = (T*)h;
+    for (int l = 0; l <= k; ++l) ho[l] = st.R[(k - 1) * SYLV_MAXV + l];
+    return SYLV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The inexact LR-ADI solver (Algorithm 1) on one GPU.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Adi : AdiBase {
+    AdiDev<T> d{};
+    Engine<T> eng;
+    cudaStream_t stream = nullptr;
+    int n = 0, m = 0, r = 0, kmax = 0, max_inner = 0;
+    Dev<double> f, g, hist;
+    Dev<T> w, t, Z, Y, gam, alpha, beta, pinvA, pinvB, gpart;
+    Dev<AdiState<T>> st;
+    int* h_done = nullptr;
+    int* d_hdone = nullptr;
+    int solved = 0;
+    int last_status = SYLV_ERR_NOT_SOLVED;
+    long long ticks = 0;
+
+    ~Adi() override {
+        if (h_done) cudaFreeHost(h_done);
+    }
+
+    int init(const AdiArgs& a) {
+        stream = a.stream;
+        n = a.n; m = a.m; r = a.r; kmax = a.o.kmax; max_inner = a.o.max_inner;
+        const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
+                                               : auto_rows_per_chunk((long long)(n + m) * r);
+        SYLV_TRY(f.alloc((size_t)n * r));
+        SYLV_TRY(g.alloc((size_t)m * r));
+        SYLV_TRY(w.alloc((size_t)n * r));
+        SYLV_TRY(t.alloc((size_t)m * r));
+        SYLV_TRY(Z.alloc((size_t)n * r * kmax));
+        SYLV_TRY(Y.alloc((size_t)m * r * kmax));
+        SYLV_TRY(gam.alloc((size_t)r * kmax));
+        SYLV_TRY(hist.alloc((size_t)kmax * SYLV_HIST_COLS));
+        SYLV_TRY(alpha.alloc(a.nshift));
+        SYLV_TRY(beta.alloc(a.nshift));
+        if (a.o.jacobi) {
+            SYLV_TRY(pinvA.alloc(n));
+            SYLV_TRY(pinvB.alloc(m));
+        }
+        SYLV_TRY(st.alloc(1));
+        SYLV_CK(cudaMemset(st.p, 0, sizeof(AdiState<T>)));
+        SYLV_CK(cudaMemset(Z.p, 0, Z.count * sizeof(T)));
+        SYLV_CK(cudaMemset(Y.p, 0, Y.count * sizeof(T)));
+        SYLV_CK(cudaMemset(hist.p, 0, hist.count * sizeof(double)));
+        std::vector<T> ha(a.nshift), hb(a.nshift);
+        for (int i = 0; i < a.nshift; ++i) {
+            ha[i] = make_scalar<T>(a.alpha[i].re, a.alpha[i].im);
+            hb[i] = make_scalar<T>(a.beta[i].re, a.beta[i].im);
+        }
+        SYLV_CK(cudaMemcpy(alpha.p, ha.data(), a.nshift * sizeof(T), cudaMemcpyHostToDevice));
+        SYLV_CK(cudaMemcpy(beta.p, hb.data(), a.nshift * sizeof(T), cudaMemcpyHostToDevice));
+        SYLV_TRY(set_rhs(a.f, a.g, 0));
+        // 2r column systems: A side uses operator 0, B side operator 1 (B^T).
+        std::vector<int> sn, so;
+        std::vector<T*> pv;
+        for (int l = 0; l < r; ++l) { sn.push_back(n); so.push_back(0); pv.push_back(pinvA.p); }
+        for (int l = 0; l < r; ++l) { sn.push_back(m); so.push_back(1); pv.push_back(pinvB.p); }
+        std::vector<OpDesc> ops{a.A->desc, a.Bt->desc};
+        SYLV_TRY(eng.setup(sn, so, ops, pv, {}, 0, a.o.restart, rpc, stream));
+        const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
+        SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
+        SYLV_CK(cudaHostAlloc((void**)&h_done, sizeof(int), cudaHostAllocMapped));
+        *h_done = 0;
+        SYLV_CK(cudaHostGetDevicePointer((void**)&d_hdone, h_done, 0));
+        d.n = n; d.m = m; d.r = r; d.kmax = kmax; d.nshift = a.nshift;
+        d.strategy = a.o.strategy; d.bl_clamp = a.o.bl_clamp; d.max_inner = max_inner;
+        d.tau = a.tau; d.xi = a.o.xi;
+        d.dminA = a.o.dmin_A; d.dminB = a.o.dmin_B; d.dmaxA = a.o.dmax_A; d.dmaxB = a.o.dmax_B;
+        d.fixed_tol = a.o.fixed_tol;
+        d.alpha = alpha.p; d.beta = beta.p;
+        d.f = f.p; d.g = g.p; d.w = w.p; d.t = t.p; d.Z = Z.p; d.Y = Y.p; d.gam = gam.p;
+        d.hist = hist.p;
+        d.diagA = a.A->desc.diag; d.diagB = a.Bt->desc.diag;
+        d.pinvA = pinvA.p; d.pinvB = pinvB.p;
+        d.sd = eng.d_sd.p; d.st = eng.d_st.p; d.ctl = eng.d_ctl.p;
+        d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
+        d.s = st.p; d.h_done = d_hdone;
+        return SYLV_OK;
+    }
+
+    int set_rhs(const double* hf, const double* hg, int on_device) override {
+        if (!hf || !hg) { set_error("set_rhs: null f or g"); return SYLV_ERR_INVALID; }
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        SYLV_CK(cudaMemcpyAsync(f.p, hf, (size_t)n * r * sizeof(double), kind, stream));
+        SYLV_CK(cudaMemcpyAsync(g.p, hg, (size_t)m * r * sizeof(double), kind, stream));
+        if (!on_device) SYLV_CK(cudaStreamSynchronize(stream));
+        return SYLV_OK;
+    }
+
+    int solve() override {
+        const int nb = d.nchA + d.nchB;
+        *h_done = 0;
+        k_adi_gram<T><<<nb, SYLV_BLOCK, 0, stream>>>(d, 1);
+        SYLV_CK(cudaGetLastError());
+        long long t0 = eng.ticks;
+        for (int step = 0; step <= kmax; ++step) {
+            SYLV_CK(cudaStreamSynchronize(stream));
+            if (*(volatile int*)h_done) break;
+            *eng.h_flag = 1;
+            k_adi_controller<T><<<1, 32, 0, stream>>>(d);
+            k_adi_step_init<T><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+            SYLV_CK(cudaGetLastError());
+            SYLV_TRY(eng.run((long long)max_inner + 8));
+            k_adi_gram<T><<<nb, SYLV_BLOCK, 0, stream>>>(d, 0);
+            SYLV_CK(cudaGetLastError());
+        }
+        SYLV_CK(cudaStreamSynchronize(stream));
+        ticks = eng.ticks - t0;
+        AdiState<T> s;
+        SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        solved = 1;
+        if (s.status == 2) { set_error("non-finite value during the solve"); last_status = SYLV_ERR_NONFINITE; }
+        else if (s.status == 1 || !s.done) { set_error("kmax outer steps without reaching tau"); last_status = SYLV_ERR_MAXIT; }
+        else if (s.stalled > 0) { set_error("%d inner solves reached max_inner", s.stalled); last_status = SYLV_ERR_INNER_STALL; }
+        else last_status = SYLV_OK;
+        return last_status;
+    }
+
+    int info(sylv_info* out) const override {
+        AdiState<T> s;
+        SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        std::memset(out, 0, sizeof(*out));
+        out->status = last_status;
+        out->steps = solved ? s.k - 1 : 0;
+        out->kr = out->steps * r;
+        out->is_complex = sizeof(T) == sizeof(cplx);
+        out->rel_res_comp = s.nfg > 0 ? s.res / s.nfg : 0.0;
+        out->norm_fg = s.nfg;
+        out->inner_its_A = s.itsA;
+        out->inner_its_B = s.itsB;
+        out->inner_restarts = s.cycles;
+        out->stalled_solves = s.stalled;
+        out->ticks = (int32_t)ticks;
+        return SYLV_OK;
+    }
+
+    int history(double* buf, int cap, int* rows) const override {
+        AdiState<T> s;
+        SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        int nrow = solved ? std::min(cap, s.k - 1) : 0;
+        if (nrow > 0)
+            SYLV_CK(cudaMemcpy(buf, hist.p, (size_t)nrow * SYLV_HIST_COLS * sizeof(double), cudaMemcpyDeviceToHost));
+        if (rows) *rows = nrow;
+        return SYLV_OK;
+    }
+
+    int factors(void* Zo, void* Yo, void* go, int on_device, int* kr) const override {
+        AdiState<T> s;
+        SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        const int steps = solved ? s.k - 1 : 0;
+        const size_t ncol = (size_t)steps * r;
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (Zo && ncol) SYLV_CK(cudaMemcpy(Zo, Z.p, ncol * n * sizeof(T), kind));
+        if (Yo && ncol) SYLV_CK(cudaMemcpy(Yo, Y.p, ncol * m * sizeof(T), kind));
+        if (go && ncol) SYLV_CK(cudaMemcpy(go, gam.p, ncol * sizeof(T), kind));
+        if (kr) *kr = (int)ncol;
+        return SYLV_OK;
+    }
+};
+
+template <typename T>
+int make_adi_t(const AdiArgs& a, AdiBase** out) {
+    Adi<T>* p = new (std::nothrow) Adi<T>();
+    if (!p) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
+    int rc = p->init(a);
+    if (rc != SYLV_OK) { delete p; return rc; }
+    *out = p;
+    return SYLV_OK;
+}
+
+}  // namespace sylv

@@ -1,0 +1,109 @@
+// internal.h - host-side declarations shared by the translation units of the
+// solver library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/sylv_adi.h"
+#include "common.cuh"
+
+namespace sylv {
+
+void set_error(const char* fmt, ...);
+
+#define SYLV_CK(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::sylv::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                              __FILE__, __LINE__);                                      \
+            return SYLV_ERR_CUDA;                                                       \
+        }                                                                               \
+    } while (0)
+
+#define SYLV_TRY(expr)            \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != SYLV_OK) return rc_; \
+    } while (0)
+
+// Host copy of a validated CSR matrix.
+struct HostCsr {
+    int n = 0;
+    std::vector<int> rp, ci;
+    std::vector<double> v;
+};
+
+int load_csr(const sylv_csr* c, HostCsr& out);
+void transpose_csr(const HostCsr& a, HostCsr& t);
+
+// Device operator owned by a sylv_op.
+struct DevOp {
+    OpDesc desc{};
+    int is_stencil = 0;
+    double* d_dval = nullptr;
+    int* d_rp = nullptr;
+    int* d_ci = nullptr;
+    double* d_v = nullptr;
+    double* d_diag = nullptr;
+    int upload(const HostCsr& h);
+    void release();
+};
+
+int num_sms();
+int auto_rows_per_chunk(long long total_rows);
+
+// Type-erased entry points implemented for double (real shifts) and cplx.
+struct AdiBase {
+    virtual ~AdiBase() {}
+    virtual int solve() = 0;
+    virtual int set_rhs(const double* f, const double* g, int on_device) = 0;
+    virtual int info(sylv_info* out) const = 0;
+    virtual int history(double* buf, int cap, int* rows) const = 0;
+    virtual int factors(void* Z, void* Y, void* gamma, int on_device, int* kr) const = 0;
+};
+
+struct AdiArgs {
+    const DevOp* A;
+    const DevOp* Bt;
+    int n, m, r;
+    const double* f;
+    const double* g;
+    const sylv_shift* alpha;
+    const sylv_shift* beta;
+    int nshift;
+    double tau;
+    sylv_opts o;
+    cudaStream_t stream;
+};
+
+int make_adi_real(const AdiArgs& a, AdiBase** out);
+int make_adi_cplx(const AdiArgs& a, AdiBase** out);
+
+int gmres_real(const DevOp& op, double sigma, int jacobi, const void* B, void* X, int ncols,
+               double tol, int restart, int max_iters, int* iters, double* res, double* hist,
+               cudaStream_t s);
+int gmres_cplx(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X, int ncols,
+               double tol, int restart, int max_iters, int* iters, double* res, double* hist,
+               cudaStream_t s);
+int cgs2_real(const void* V, int n, int k, void* w, void* h, cudaStream_t s);
+int cgs2_cplx(const void* V, int n, int k, void* w, void* h, cudaStream_t s);
+int op_apply_real(const DevOp& op, double sigma, int jacobi, const void* X, void* Y, int ncols, cudaStream_t s);
+int op_apply_cplx(const DevOp& op, sylv_shift sigma, int jacobi, const void* X, void* Y, int ncols, cudaStream_t s);
+int controller_eval_dev(const sylv_opts* o, int count, const double* in, double* out);
+
+}  // namespace sylv
+
+struct sylv_op {
+    sylv::DevOp op;
+};
+
+struct sylv_handle {
+    sylv::AdiBase* impl = nullptr;
+    sylv::DevOp A, Bt;
+    int is_complex = 0;
+    int solved = 0;
+    int last_status = SYLV_ERR_NOT_SOLVED;
+    cudaStream_t stream = nullptr;
+};

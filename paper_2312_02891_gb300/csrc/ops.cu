@@ -1,0 +1,173 @@
+// ops.cu - host handling of the sparse operators: CSR validation, the
+// transpose needed for (B + alpha I)^* = B^T + conj(alpha) I (real B), the
+// diagonal extraction for the Jacobi preconditioner, and the choice of
+// storage: by diagonals when the nonzeros lie on at most SYLV_MAXDIAG fixed
+// offsets (the finite-difference stencils of the paper's convection-diffusion
+// examples), CSR otherwise.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include "internal.h"
+
+namespace sylv {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char* last_error_cstr() { return g_err.c_str(); }
+
+int num_sms() {
+    static int cached = 0;
+    if (cached) return cached;
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+        cached = v;
+    else
+        return 152;
+    return cached;
+}
+
+int auto_rows_per_chunk(long long total_rows) {
+    // Aim at about four work units per SM across the whole batch, in whole
+    // multiples of the block size.
+    long long target = (total_rows + (long long)num_sms() * 4 - 1) / ((long long)num_sms() * 4);
+    target = (target + SYLV_BLOCK - 1) / SYLV_BLOCK * SYLV_BLOCK;
+    return (int)std::max<long long>(512, std::min<long long>(target, 1 << 16));
+}
+
+int load_csr(const sylv_csr* c, HostCsr& h) {
+    if (!c) { set_error("null CSR descriptor"); return SYLV_ERR_INVALID; }
+    if (c->n_rows <= 0 || c->n_rows != c->n_cols) {
+        set_error("CSR must be square with n > 0 (got %d x %d)", c->n_rows, c->n_cols);
+        return SYLV_ERR_INVALID;
+    }
+    if (c->nnz < 0 || c->nnz > 0x7fffffffLL) { set_error("CSR nnz out of range"); return SYLV_ERR_INVALID; }
+    if (!c->rowptr || (c->nnz > 0 && (!c->colind || !c->val))) {
+        set_error("CSR has null arrays");
+        return SYLV_ERR_INVALID;
+    }
+    const int n = c->n_rows;
+    const size_t nnz = (size_t)c->nnz;
+    h.n = n;
+    h.rp.resize(n + 1);
+    h.ci.resize(nnz);
+    h.v.resize(nnz);
+    if (c->on_device) {
+        SYLV_CK(cudaMemcpy(h.rp.data(), c->rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+        if (nnz) {
+            SYLV_CK(cudaMemcpy(h.ci.data(), c->colind, nnz * sizeof(int), cudaMemcpyDeviceToHost));
+            SYLV_CK(cudaMemcpy(h.v.data(), c->val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+    } else {
+        std::memcpy(h.rp.data(), c->rowptr, (n + 1) * sizeof(int));
+        if (nnz) {
+            std::memcpy(h.ci.data(), c->colind, nnz * sizeof(int));
+            std::memcpy(h.v.data(), c->val, nnz * sizeof(double));
+        }
+    }
+    if (h.rp[0] != 0 || (size_t)h.rp[n] != nnz) {
+        set_error("CSR rowptr must start at 0 and end at nnz");
+        return SYLV_ERR_INVALID;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (h.rp[i + 1] < h.rp[i]) { set_error("CSR rowptr decreases at row %d", i); return SYLV_ERR_INVALID; }
+        for (int p = h.rp[i]; p < h.rp[i + 1]; ++p)
+            if (h.ci[p] < 0 || h.ci[p] >= n) {
+                set_error("CSR column index %d out of range in row %d", h.ci[p], i);
+                return SYLV_ERR_INVALID;
+            }
+    }
+    return SYLV_OK;
+}
+
+void transpose_csr(const HostCsr& a, HostCsr& t) {
+    const int n = a.n;
+    t.n = n;
+    t.rp.assign(n + 1, 0);
+    t.ci.resize(a.ci.size());
+    t.v.resize(a.v.size());
+    for (size_t p = 0; p < a.ci.size(); ++p) t.rp[a.ci[p] + 1]++;
+    for (int i = 0; i < n; ++i) t.rp[i + 1] += t.rp[i];
+    std::vector<int> pos(t.rp.begin(), t.rp.end() - 1);
+    for (int i = 0; i < n; ++i)
+        for (int p = a.rp[i]; p < a.rp[i + 1]; ++p) {
+            const int q = pos[a.ci[p]]++;
+            t.ci[q] = i;
+            t.v[q] = a.v[p];
+        }
+}
+
+void DevOp::release() {
+    if (d_dval) cudaFree(d_dval);
+    if (d_rp) cudaFree(d_rp);
+    if (d_ci) cudaFree(d_ci);
+    if (d_v) cudaFree(d_v);
+    if (d_diag) cudaFree(d_diag);
+    d_dval = d_v = d_diag = nullptr;
+    d_rp = d_ci = nullptr;
+}
+
+int DevOp::upload(const HostCsr& h) {
+    release();
+    const int n = h.n;
+    std::vector<double> diag(n, 0.0);
+    std::map<int, int> offs;
+    bool stencil = true;
+    for (int i = 0; i < n; ++i)
+        for (int p = h.rp[i]; p < h.rp[i + 1]; ++p) {
+            const int o = h.ci[p] - i;
+            if (o == 0) diag[i] += h.v[p];
+            if (stencil && !offs.count(o)) {
+                if ((int)offs.size() >= SYLV_MAXDIAG) stencil = false;
+                else offs[o] = 0;
+            }
+        }
+    desc = OpDesc{};
+    desc.n = n;
+    if (stencil) {
+        int d = 0;
+        for (auto& kv : offs) { kv.second = d; desc.offs[d] = kv.first; ++d; }
+        desc.ndiag = d;
+        desc.fmt = 1;
+        std::vector<double> dval((size_t)d * n, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int p = h.rp[i]; p < h.rp[i + 1]; ++p)
+                dval[(size_t)offs[h.ci[p] - i] * n + i] += h.v[p];
+        if (d > 0) {
+            SYLV_CK(cudaMalloc((void**)&d_dval, dval.size() * sizeof(double)));
+            SYLV_CK(cudaMemcpy(d_dval, dval.data(), dval.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        desc.dval = d_dval;
+    } else {
+        desc.fmt = 0;
+        SYLV_CK(cudaMalloc((void**)&d_rp, (n + 1) * sizeof(int)));
+        SYLV_CK(cudaMemcpy(d_rp, h.rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        if (!h.ci.empty()) {
+            SYLV_CK(cudaMalloc((void**)&d_ci, h.ci.size() * sizeof(int)));
+            SYLV_CK(cudaMalloc((void**)&d_v, h.v.size() * sizeof(double)));
+            SYLV_CK(cudaMemcpy(d_ci, h.ci.data(), h.ci.size() * sizeof(int), cudaMemcpyHostToDevice));
+            SYLV_CK(cudaMemcpy(d_v, h.v.data(), h.v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        desc.rowptr = d_rp;
+        desc.colind = d_ci;
+        desc.val = d_v;
+    }
+    is_stencil = stencil ? 1 : 0;
+    SYLV_CK(cudaMalloc((void**)&d_diag, n * sizeof(double)));
+    SYLV_CK(cudaMemcpy(d_diag, diag.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    desc.diag = d_diag;
+    return SYLV_OK;
+}
+
+}  // namespace sylv

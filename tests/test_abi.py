@@ -1,0 +1,87 @@
+"""The C ABI library loads and exports every entry point declared in
+include/sylv_adi.h; host-side argument checks that need no GPU."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import paper_2312_02891_gb300 as P
+
+HEADER = Path(__file__).resolve().parents[1] / "include" / "sylv_adi.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(sylv_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ("sylv_adi_create", "sylv_adi_solve", "sylv_adi_factors", "sylv_op_apply",
+                 "sylv_cgs2", "sylv_gmres", "sylv_controller_eval"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(P.EXPORTED) == declared_functions()
+
+
+def test_opts_default_matches_paper_settings(lib):
+    o = P.sylv_opts_default()
+    assert o.xi == 1.0 and o.kmax == 50 and o.dmax_A == 0.1 and o.dmax_B == 0.1
+    assert o.strategy == P.STRATEGIES["bl_mid"] and o.restart == 30
+
+
+def _csr_struct(n, rp, ci, v):
+    rp = np.asarray(rp, np.int32); ci = np.asarray(ci, np.int32); v = np.asarray(v, np.float64)
+    return (rp, ci, v), P.SylvCsr(n, n, int(rp[-1]) if len(rp) else 0, rp.ctypes.data,
+                                  ci.ctypes.data, v.ctypes.data, 0)
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    out = C.c_void_p()
+    # non-square
+    keep, s = _csr_struct(2, [0, 1, 2], [0, 1], [1.0, 1.0])
+    s.n_cols = 3
+    assert lib.sylv_op_create(C.byref(s), 0, C.byref(out)) == -1
+    # column out of range
+    keep, s = _csr_struct(2, [0, 1, 2], [0, 5], [1.0, 1.0])
+    assert lib.sylv_op_create(C.byref(s), 0, C.byref(out)) == -1
+    assert "out of range" in P.sylv_last_error()
+    # decreasing rowptr
+    keep, s = _csr_struct(2, [0, 2, 1], [0, 1], [1.0, 1.0])
+    assert lib.sylv_op_create(C.byref(s), 0, C.byref(out)) == -1
+    # null descriptor
+    assert lib.sylv_op_create(None, 0, C.byref(out)) == -1
+    # adi_create: rank 0 and rank above the build limit
+    keep, s = _csr_struct(2, [0, 1, 2], [0, 1], [-1.0, -2.0])
+    f = np.ones(2)
+    sh = (P.SylvShift * 1)(P.SylvShift(-1.0, 0.0))
+    pd = f.ctypes.data_as(C.POINTER(C.c_double))
+    assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 0, sh, sh, 1, 1e-8, None, None, C.byref(out)) == -1
+    assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 5, sh, sh, 1, 1e-8, None, None, C.byref(out)) == -8
+    # tolerance outside (0, 1)
+    assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 1, sh, sh, 1, 0.0, None, None, C.byref(out)) == -1
+    # unpaired complex shift
+    shc = (P.SylvShift * 1)(P.SylvShift(-1.0, 1.0))
+    assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 1, shc, shc, 1, 1e-8, None, None, C.byref(out)) == -1
+    assert "conjugate" in P.sylv_last_error()
+    # restart beyond the build limit
+    o = P.sylv_opts_default(restart=31)
+    assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 1, sh, sh, 1, 1e-8, C.byref(o), None, C.byref(out)) == -8
+
+
+def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
+    """No CPU fallback: a missing shared library is an error."""
+    import importlib
+    mod = importlib.reload(P)
+    monkeypatch.setattr(mod, "lib_path", lambda: tmp_path / "missing.so")
+    monkeypatch.setattr(mod, "_LIB", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mod.load()
+    importlib.reload(P)

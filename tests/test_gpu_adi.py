@@ -1,0 +1,133 @@
+"""End-to-end parity of the GPU inexact LR-ADI (Algorithm 1) with the oracle
+through the C ABI: outer step counts, per-step controller history, the
+computed and true residuals, and the factored solution X = Z Gamma Y^*."""
+import numpy as np
+import pytest
+
+import paper_2312_02891_gb300 as P
+from paper_2312_02891_gb300 import workloads as W
+from oracle.dense import bartels_stewart
+from oracle.lradi import lradi
+from oracle.residual import factored_diff_fro, factored_fro, lowrank_norm2, true_residual_norm2
+
+pytestmark = pytest.mark.gpu
+
+_PROB = {}
+
+
+def problem(name):
+    if name not in _PROB:
+        _PROB[name] = W.problem_config(name)
+    return _PROB[name]
+
+
+def run_gpu(p, **opts):
+    with P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, **opts) as s:
+        st = s.solve()
+        info = s.info()
+        hist = s.history()
+        Z, Y, gam = s.factors()
+    return st, info, hist, Z, Y, gam
+
+
+def compare(p, strategy, jacobi, xtol=1e-6, **extra):
+    st, info, hist, Z, Y, gam = run_gpu(p, strategy=strategy, jacobi=int(jacobi), **extra)
+    ref = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy=strategy, jacobi=jacobi,
+                **{k: v for k, v in extra.items() if k in ("kmax", "xi", "fixed_tol", "max_inner", "restart")})
+    A, B = p.A.to_scipy(), p.B.to_scipy()
+    nfg = lowrank_norm2(p.f, p.g)
+    assert st == 0, P.sylv_last_error()
+    assert ref.converged
+    # outer iteration counts within +-1
+    assert abs(info["steps"] - ref.steps) <= 1, (info["steps"], ref.steps)
+    # computed relative residual below tau on both
+    assert info["rel_res_comp"] < p.tau and ref.res_comp < p.tau
+    # ||f g^*|| agrees
+    assert info["norm_fg"] == pytest.approx(nfg, rel=1e-12)
+    # true residuals through the factors, GPU vs oracle
+    tr_gpu = true_residual_norm2(A, B, p.f, p.g, Z, gam, Y) / nfg
+    tr_ref = true_residual_norm2(A, B, p.f, p.g, ref.Z, ref.gamma, ref.Y) / nfg
+    assert tr_gpu <= max(1.5 * tr_ref, 1e-8), (tr_gpu, tr_ref)
+    # factored solutions agree
+    dX = factored_diff_fro(Z, gam, Y, ref.Z, ref.gamma, ref.Y) / factored_fro(ref.Z, ref.gamma, ref.Y)
+    assert dX <= xtol, dX
+    # step-by-step history over the common steps: shifts, tolerances, residuals
+    ks = min(len(hist), len(ref.history))
+    for i in range(ks):
+        h, o = hist[i], ref.history[i]
+        assert h[0] == o["k"]
+        assert h[1] == pytest.approx(np.real(o["alpha"])) and h[2] == pytest.approx(np.real(o["beta"]))
+        assert h[3] == pytest.approx(o["dA"], rel=1e-3) and h[4] == pytest.approx(o["dB"], rel=1e-3)
+        assert h[12] == pytest.approx(o["res_comp"], rel=1e-3, abs=1e-3 * p.tau)
+        assert h[13] == pytest.approx(o["N_w"], rel=1e-6)
+    return info, ref, tr_gpu, tr_ref, dX
+
+
+@pytest.mark.parametrize("strategy", ["bl_mid", "nobl_mid", "fixed", "bl_B", "nobl_A"])
+def test_small2d_parity(strategy):
+    p = problem("small2d")
+    info, ref, tr_gpu, tr_ref, dX = compare(p, strategy, jacobi=False)
+    # the paper's qualitative point: dynamic tolerances need fewer inner steps than fixed ones
+    if strategy == "bl_mid":
+        fixed = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy="fixed")
+        assert info["inner_its_A"] + info["inner_its_B"] < fixed.inner_its_A + fixed.inner_its_B
+
+
+def test_small2d_against_bartels_stewart():
+    p = problem("small2d")
+    st, info, hist, Z, Y, gam = run_gpu(p, strategy="nobl_mid", jacobi=0)
+    X = bartels_stewart(p.A.to_scipy(), p.B.to_scipy(), p.f, p.g)
+    err = np.linalg.norm(Z @ np.diag(gam) @ Y.T - X) / np.linalg.norm(X)
+    assert err < 1e-6
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_tiny2d_rank2_parity(jacobi):
+    compare(problem("tiny2d"), "bl_mid", jacobi)
+
+
+def test_rank3_ragged_parity():
+    p = W.make_problem("r3", 19, 2, "xy", 20.0, 13, 2, "rot2", 8.0, 3, 21, 10)
+    compare(p, "bl_mid", True)
+
+
+def test_complex_shift_pairs_parity():
+    # rotational convection on both sides: complex Ritz values, conjugate pairs kept
+    p = W.make_problem("cplx", 14, 2, "rot2", 60.0, 12, 2, "rot2", 40.0, 2, 33, 8, real_shifts=False)
+    assert np.iscomplexobj(p.alpha) and np.any(np.imag(p.alpha) != 0)
+    info, ref, tr_gpu, tr_ref, dX = compare(p, "bl_mid", True)
+    assert info["is_complex"] == 1
+
+
+def test_zero_rhs_is_solved_by_zero():
+    p = problem("tiny2d")
+    z = np.zeros_like(p.f)
+    with P.SylvesterADI(p.A, p.B, z, p.g, p.alpha, p.beta, p.tau) as s:
+        assert s.solve() == 0
+        assert s.info()["steps"] == 0
+
+
+def test_kmax_reached_returns_maxit():
+    p = problem("small2d")
+    with P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, kmax=3, jacobi=0) as s:
+        assert s.solve() == -4
+        info = s.info()
+        assert info["steps"] == 3 and info["kr"] == 3
+        Z, Y, gam = s.factors()
+        assert Z.shape == (p.A.n, 3)
+    ref = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, kmax=3)
+    assert ref.steps == 3 and not ref.converged
+
+
+def test_resolve_with_new_rhs_is_repeatable():
+    p = problem("tiny2d")
+    with P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau) as s:
+        s.solve()
+        Z1, Y1, g1 = s.factors()
+        f2, g2 = W.rhs_factors(p.A.n, p.B.n, p.r, 99)
+        s.set_rhs(f2, g2)
+        s.solve()
+        s.set_rhs(p.f, p.g)
+        s.solve()
+        Z2, Y2, g2_ = s.factors()
+    assert np.array_equal(Z1, Z2) and np.array_equal(Y1, Y2) and np.array_equal(g1, g2_)
