@@ -54,7 +54,11 @@ extern "C" {
 #define SYLV_STRAT_BL_B         6
 
 /* ---- precision of the inner Krylov solves ---- */
-#define SYLV_PREC_FP64          0   /* everything in float64 */
+#define SYLV_PREC_FP64          0   /* everything in float64 (complex128 for complex shifts) */
+#define SYLV_PREC_FP32          1   /* Krylov basis and its sweeps in float32 (complex64); the
+                                       restart residual, the Hessenberg least squares, the
+                                       solutions, the factors and the outer iteration in float64 */
+#define SYLV_PREC_BF16          2   /* as FP32 with the Krylov basis stored in bfloat16 */
 
 /* Sparse square matrix in CSR form.  Borrowed; copied by the create calls. */
 typedef struct sylv_csr {
@@ -86,6 +90,10 @@ typedef struct sylv_opts {
     int32_t bl_clamp;            /* 0: eq. (ADI_relax2_prak) literally, |.|;
                                     1: max(., 0) in place of |.| (paper silent) */
     int32_t rows_per_chunk;      /* work-unit size of the vector kernels; 0 = auto */
+    int32_t driver;              /* 0: each solve is one CUDA graph whose conditional nodes
+                                    the kernels set (no host round trip inside a solve);
+                                    1: the host launches every device iteration.  Profiling
+                                    (sylv_adi_profile) always uses the host-driven loop. */
 } sylv_opts;
 
 #define SYLV_MAX_RESTART 30
@@ -103,6 +111,7 @@ typedef struct sylv_info {
     int64_t inner_restarts;      /* GMRES cycles over all solves */
     int32_t stalled_solves;      /* inner solves that hit max_inner */
     int32_t ticks;               /* device iterations launched (for diagnostics) */
+    int64_t launches;            /* kernel launches of the last solve */
 } sylv_info;
 
 /* Columns of one row of sylv_adi_history() (doubles, row-major). */
@@ -167,10 +176,13 @@ int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out,
  * iters_out (Arnoldi steps), resnorm_out (true residual norms).
  * Returns SYLV_ERR_INNER_STALL if some column stopped at max_iters.
  * Optional hist_out (host, ncols x max_iters doubles, may be NULL): the Givens
- * residual estimate after each Arnoldi step. */
+ * residual estimate after each Arnoldi step.  precision = SYLV_PREC_*: with
+ * FP32/BF16 the basis and its sweeps run in float32 while B, X, the restart
+ * residual and the least squares stay float64 (iterative refinement across
+ * restarts), so tol is still met in float64. */
 int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
                const void* B, void* X, int32_t ncols, double tol, int32_t restart,
-               int32_t max_iters, int32_t* iters_out, double* resnorm_out,
+               int32_t max_iters, int32_t precision, int32_t* iters_out, double* resnorm_out,
                double* hist_out, void* stream);
 
 /* ------------------------------------------------------------------------ */
@@ -218,6 +230,23 @@ int sylv_adi_history(const sylv_handle* h, double* buf, int32_t cap, int32_t* ro
 int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_t on_device,
                      int32_t* kr_out, int32_t* is_complex);
 int sylv_adi_destroy(sylv_handle* h);
+
+/* Kernel statistics of a handle.  SYLV_NUM_KERNELS entries, in this order:
+ * shifted product + first Gram-Schmidt sweep, second sweep, third sweep with
+ * the Givens update, restart update, restart residual, controller,
+ * step initialisation, factor update + Gram.  sylv_adi_profile(h, 1) resets
+ * the counters and times the launches of every fourth device iteration (and
+ * every outer-step kernel) with CUDA events on the handle's stream; 0 stops
+ * the timing and resets too.  sylv_adi_kernel_stats copies, per kernel, the
+ * estimated milliseconds (mean event-timed duration of the timed launches
+ * times the number of launches; 0 when not profiling), the algorithmic bytes
+ * moved and floating-point operations (accumulated by the kernels from each
+ * system's size, Krylov index and the matrix's nonzeros) and the number of
+ * launches, since the last reset.  Any pointer may be NULL. */
+#define SYLV_NUM_KERNELS 8
+int sylv_adi_profile(sylv_handle* h, int32_t enable);
+int sylv_adi_kernel_stats(const sylv_handle* h, double* ms, double* bytes, double* flops,
+                          int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ __all__ = [
     "sylv_op_apply", "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval",
     "sylv_adi_create", "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve",
     "sylv_adi_info", "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "SylvesterADI",
-    "HIST_COLUMNS", "EXPORTED",
+    "sylv_adi_profile", "sylv_adi_kernel_stats", "HIST_COLUMNS", "EXPORTED", "KERNELS",
 ]
 
 SYLV_OK = 0
@@ -29,14 +29,18 @@ ERRORS = {-1: "INVALID", -2: "CUDA", -3: "NOMEM", -4: "MAXIT", -5: "INNER_STALL"
           -6: "NONFINITE", -7: "NOT_SOLVED", -8: "UNSUPPORTED"}
 WARNINGS = (-4, -5)      # solve finished, factors valid
 STRATEGIES = {"fixed": 0, "nobl_mid": 1, "bl_mid": 2, "nobl_A": 3, "bl_A": 4, "nobl_B": 5, "bl_B": 6}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 HIST_COLUMNS = ("k", "alpha", "beta", "dA", "dB", "eps_hat", "nrA", "nrB", "itsA", "itsB",
                 "u", "v", "res_comp", "N_w")
 EXPORTED = (
     "sylv_last_error", "sylv_opts_default", "sylv_op_create", "sylv_op_format", "sylv_op_apply",
     "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval", "sylv_adi_create",
     "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
-    "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy",
+    "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "sylv_adi_profile",
+    "sylv_adi_kernel_stats",
 )
+KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3", "restart_update", "restart_residual",
+           "adi_controller", "adi_step_init", "adi_gram")
 
 
 class SylvError(RuntimeError):
@@ -60,7 +64,7 @@ class SylvOpts(C.Structure):
                 ("dmax_A", C.c_double), ("dmax_B", C.c_double), ("kmax", C.c_int32),
                 ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
-                ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32)]
+                ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32)]
 
 
 class SylvInfo(C.Structure):
@@ -68,7 +72,7 @@ class SylvInfo(C.Structure):
                 ("is_complex", C.c_int32), ("rel_res_comp", C.c_double), ("norm_fg", C.c_double),
                 ("inner_its_A", C.c_int64), ("inner_its_B", C.c_int64),
                 ("inner_restarts", C.c_int64), ("stalled_solves", C.c_int32),
-                ("ticks", C.c_int32)]
+                ("ticks", C.c_int32), ("launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,7 +105,7 @@ def load():
         "sylv_op_apply": ([vp, SylvShift, i32, i32, vp, vp, i32, vp], C.c_int),
         "sylv_op_destroy": ([vp], C.c_int),
         "sylv_cgs2": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
-        "sylv_gmres": ([vp, SylvShift, i32, i32, vp, vp, i32, d, i32, i32, pi32, pd, pd, vp], C.c_int),
+        "sylv_gmres": ([vp, SylvShift, i32, i32, vp, vp, i32, d, i32, i32, i32, pi32, pd, pd, vp], C.c_int),
         "sylv_controller_eval": ([C.POINTER(SylvOpts), i32, pd, pd], C.c_int),
         "sylv_adi_create": ([C.POINTER(SylvCsr), C.POINTER(SylvCsr), pd, pd, i32,
                              C.POINTER(SylvShift), C.POINTER(SylvShift), i32, d,
@@ -113,6 +117,8 @@ def load():
         "sylv_adi_history": ([vp, pd, i32, pi32], C.c_int),
         "sylv_adi_factors": ([vp, vp, vp, vp, i32, pi32, pi32], C.c_int),
         "sylv_adi_destroy": ([vp], C.c_int),
+        "sylv_adi_profile": ([vp, i32], C.c_int),
+        "sylv_adi_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -164,6 +170,8 @@ def sylv_opts_default(**overrides) -> SylvOpts:
     for k, v in overrides.items():
         if k == "strategy" and isinstance(v, str):
             v = STRATEGIES[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
@@ -218,13 +226,14 @@ def sylv_cgs2(V, n, k, w, is_complex=False, stream=None) -> np.ndarray:
 
 
 def sylv_gmres(op, sigma, jacobi, is_complex, B, X, ncols, tol, restart, max_iters,
-               want_hist=False, stream=None):
+               want_hist=False, stream=None, precision="fp64"):
     """Returns (status, iters[ncols], resnorm[ncols], hist or None)."""
     iters = np.zeros(ncols, dtype=np.int32)
     res = np.zeros(ncols)
     hist = np.zeros((ncols, max_iters)) if want_hist else None
     rc = load().sylv_gmres(op, _shift(sigma), int(jacobi), int(is_complex), _ptr(B), _ptr(X),
                            int(ncols), float(tol), int(restart), int(max_iters),
+                           PRECISIONS.get(precision, precision),
                            iters.ctypes.data_as(C.POINTER(C.c_int32)),
                            res.ctypes.data_as(C.POINTER(C.c_double)),
                            hist.ctypes.data_as(C.POINTER(C.c_double)) if want_hist else None,
@@ -309,6 +318,23 @@ def sylv_adi_destroy(h) -> None:
     _check(load().sylv_adi_destroy(h))
 
 
+def sylv_adi_profile(h, enable: bool) -> None:
+    _check(load().sylv_adi_profile(h, int(enable)))
+
+
+def sylv_adi_kernel_stats(h) -> dict:
+    """{kernel: (ms, algorithmic bytes, algorithmic flops, launches)} since the last reset."""
+    ms = np.zeros(len(KERNELS))
+    by = np.zeros(len(KERNELS))
+    fl = np.zeros(len(KERNELS))
+    la = np.zeros(len(KERNELS), dtype=np.int64)
+    _check(load().sylv_adi_kernel_stats(h, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                        by.ctypes.data_as(C.POINTER(C.c_double)),
+                                        fl.ctypes.data_as(C.POINTER(C.c_double)),
+                                        la.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {k: (float(ms[i]), float(by[i]), float(fl[i]), int(la[i])) for i, k in enumerate(KERNELS)}
+
+
 class SylvesterADI:
     """A X + X B = -f g^* solved on the GPU by the inexact LR-ADI iteration."""
 
@@ -333,6 +359,12 @@ class SylvesterADI:
 
     def factors(self):
         return sylv_adi_factors(self.h, self.n, self.m)
+
+    def profile(self, enable: bool = True) -> None:
+        sylv_adi_profile(self.h, enable)
+
+    def kernel_stats(self) -> dict:
+        return sylv_adi_kernel_stats(self.h)
 
     def close(self) -> None:
         if self.h:

@@ -71,7 +71,7 @@ struct AdiState {
     long long itsA, itsB, cycles;
 };
 
-template <typename T>
+template <typename T, typename S, typename C>
 struct AdiDev {
     int n, m, r, kmax, nshift, strategy, bl_clamp, max_inner;
     double tau, xi, dminA, dminB, dmaxA, dmaxB, fixed_tol;
@@ -85,11 +85,12 @@ struct AdiDev {
     T* Y;                   // m x kmax r
     T* gam;                 // kmax r
     double* hist;           // kmax x SYLV_HIST_COLS
-    const double* diagA;
-    const double* diagB;
+    OpDesc opA, opB;        // A and B^T (float64)
     T* pinvA;               // null: no preconditioner
     T* pinvB;
-    const SysDesc<T>* sd;   // systems 0..r-1: A side, r..2r-1: B side
+    C* avalA;               // pre-scaled stencil diagonals for the current shift, or null
+    C* avalB;
+    const SysDesc<T, S, C>* sd;   // systems 0..r-1: A side, r..2r-1: B side
     SysState<T>* st;
     BatchCtl* ctl;
     T* gpart;               // (nchA + nchB) x SYLV_GSTRIDE
@@ -184,15 +185,22 @@ __device__ __forceinline__ bool is_pair_start(const T* alpha, const T* beta, int
 }
 
 // Start of outer step k: tolerances, shifts and the 2r column solves.
-template <typename T>
-__global__ void k_adi_controller(AdiDev<T> d) {
+template <typename T, typename S, typename C>
+__global__ void k_adi_controller(AdiDev<T, S, C> d) {
+    count_launch(d.ctl, K_CTRL);
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     AdiState<T>* s = d.s;
     const int r = d.r;
+    // graph-driven solve: no further outer step unless the factor update asks
+    if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_outer, 0u);
     if (s->done) {
         for (int q = 0; q < 2 * r; ++q) d.st[q].phase = PH_DONE;
         d.ctl->n_active = 0;
         if (d.ctl->h_flag) { *(volatile int*)d.ctl->h_flag = 0; __threadfence_system(); }
+        if (d.ctl->graph) {
+            cudaGraphSetConditional(d.ctl->h_loop, 0u);
+            cudaGraphSetConditional(d.ctl->h_outer, 0u);
+        }
         return;
     }
     const int k = s->k;
@@ -226,12 +234,16 @@ __global__ void k_adi_controller(AdiDev<T> d) {
         }
     }
     d.ctl->n_active = 2 * r;
+    d.ctl->ticks = 0;
+    if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_loop, 1u);
 }
 
 // Per-step set-up over the rows of both sides: zero the solution slots of
-// Z and Y, and form the Jacobi inverse 1 / (diag + sigma) for the new shift.
-template <typename T>
-__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T> d) {
+// Z and Y, form the Jacobi inverse 1 / (diag + sigma) for the new shift and
+// the pre-scaled stencil diagonals of (Op + sigma I) P^{-1}.
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T, S, C> d) {
+    count_launch(d.ctl, K_STEP);
     const AdiState<T>* s = d.s;
     if (s->done) return;
     const bool sideA = (int)blockIdx.x < d.nchA;
@@ -240,12 +252,16 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T> d) {
     const int r0 = chunk * d.rpc, r1 = min(nn, r0 + d.rpc);
     const T sigma = sideA ? s->beta_k : conjg(s->alpha_k);
     T* pinv = sideA ? d.pinvA : d.pinvB;
-    const double* diag = sideA ? d.diagA : d.diagB;
+    C* aval = sideA ? d.avalA : d.avalB;
+    const OpDesc& op = sideA ? d.opA : d.opB;
     T* X = (sideA ? d.Z : d.Y) + (size_t)(s->k - 1) * d.r * nn;
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        if (pinv) pinv[i] = sdiv(make_scalar<T>(1.0, 0.0), diag[i] + sigma);
+    count_work(d.ctl, K_STEP, chunk,
+               (double)d.r * nn * sizeof(T) + (pinv ? (double)nn * (sizeof(T) + sizeof(double)) : 0.0) +
+               (aval ? (double)op.ndiag * nn * (sizeof(double) + sizeof(C)) : 0.0),
+               FmaFlops<T>::v * (aval ? (double)op.ndiag * nn : 0.0));
+    shifted_op_rows<T, C>(op, sigma, pinv, aval, r0, r1);
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
         for (int l = 0; l < d.r; ++l) X[(size_t)l * nn + i] = zero<T>();
-    }
 }
 
 // Gram partials of three n x r blocks (P, Q, R): G[a][b] = sum_i conj(P_a) P_b.
@@ -262,8 +278,9 @@ __device__ __forceinline__ void gram_acc(T* G, const T* v, int r) {
 // Gamma), then the residual norm ||w_k t_k^*|| = sqrt(lambda_max(G_w G_t)),
 // eq. (upd_resgap) and the outer stop test ||w_k t_k^*|| < tau ||f g^*||.
 // init = 1: w_0 = f, t_0 = g and the norms of the right-hand side.
-template <typename T>
-__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T> d, int init) {
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int init) {
+    count_launch(d.ctl, K_GRAM);
     AdiState<T>* s = d.s;
     if (!init && s->done) return;
     const bool sideA = (int)blockIdx.x < d.nchA;
@@ -272,6 +289,10 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T> d, int init) 
     const int r = d.r;
     const int r0 = chunk * d.rpc, r1 = min(nn, r0 + d.rpc);
     T* W = sideA ? d.w : d.t;
+    // w, z, r^A read; w written; three r x r Grams
+    count_work(d.ctl, K_GRAM, chunk,
+               init ? (double)r * nn * (sizeof(double) + sizeof(T)) : 4.0 * r * nn * sizeof(T),
+               FmaFlops<T>::v * (init ? 1.0 : 3.0) * r * r * nn);
     T G[3 * SYLV_MAXR * SYLV_MAXR];
 #pragma unroll
     for (int q = 0; q < 3 * SYLV_MAXR * SYLV_MAXR; ++q) G[q] = zero<T>();
@@ -291,14 +312,14 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T> d, int init) 
     } else {
         const T gm = sideA ? s->gamma_k : conjg(s->gamma_k);
         const T* X = (sideA ? d.Z : d.Y) + (size_t)(s->k - 1) * r * nn;
-        const SysDesc<T>* sd = d.sd + (sideA ? 0 : r);
+        const SysDesc<T, S, C>* sd = d.sd + (sideA ? 0 : r);
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             T wv[SYLV_MAXR], zv[SYLV_MAXR], rv[SYLV_MAXR];
 #pragma unroll
             for (int l = 0; l < SYLV_MAXR; ++l) {
                 if (l < r) {
                     zv[l] = X[(size_t)l * nn + i];
-                    rv[l] = sd[l].V[i];
+                    rv[l] = cvt<T>(sd[l].V[i]);
                     wv[l] = W[(size_t)l * nn + i] + gm * zv[l];
                     W[(size_t)l * nn + i] = wv[l];
                 }
@@ -308,7 +329,7 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T> d, int init) 
             gram_acc(G + 2 * SYLV_MAXR * SYLV_MAXR, rv, r);
         }
     }
-    block_reduce_store<T, 3 * SYLV_MAXR * SYLV_MAXR>(G, 3 * SYLV_MAXR * SYLV_MAXR,
+    block_reduce_store<T, T, 3 * SYLV_MAXR * SYLV_MAXR>(G, 3 * SYLV_MAXR * SYLV_MAXR,
                                                       d.gpart + (size_t)blockIdx.x * SYLV_GSTRIDE);
     if (!last_block(&s->counter, d.nchA + d.nchB)) return;
     __shared__ T GA[SYLV_GSTRIDE], GB[SYLV_GSTRIDE];
@@ -367,6 +388,7 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T> d, int init) 
         else if (s->k > d.kmax) { s->done = 1; s->status = 1; }
     }
     if (d.h_done) { *(volatile int*)d.h_done = s->done; __threadfence_system(); }
+    if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_outer, s->done ? 0u : 1u);
 }
 
 }  // namespace sylv

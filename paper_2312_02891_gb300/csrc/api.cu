@@ -32,6 +32,7 @@ int sylv_opts_default(sylv_opts* o) {
     o->jacobi = 1;
     o->bl_clamp = 0;
     o->rows_per_chunk = 0;
+    o->driver = 1;
     return SYLV_OK;
 }
 
@@ -81,17 +82,16 @@ int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out, int32_t
 
 int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
                const void* B, void* X, int32_t ncols, double tol, int32_t restart,
-               int32_t max_iters, int32_t* iters_out, double* resnorm_out, double* hist_out,
-               void* stream) {
+               int32_t max_iters, int32_t precision, int32_t* iters_out, double* resnorm_out,
+               double* hist_out, void* stream) {
     if (!op) { set_error("sylv_gmres: null op"); return SYLV_ERR_INVALID; }
     if (!(tol >= 0.0)) { set_error("sylv_gmres: tol must be >= 0"); return SYLV_ERR_INVALID; }
+    if (!is_complex && shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (is_complex)
-        return gmres_cplx(op->op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters_out,
-                          resnorm_out, hist_out, s);
-    if (shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
-    return gmres_real(op->op, sigma.re, jacobi, B, X, ncols, tol, restart, max_iters, iters_out,
-                      resnorm_out, hist_out, s);
+    auto fn = is_complex ? (precision == SYLV_PREC_FP32 ? gmres_c64 : precision == SYLV_PREC_BF16 ? gmres_cbf : gmres_c128)
+                         : (precision == SYLV_PREC_FP32 ? gmres_r32 : precision == SYLV_PREC_BF16 ? gmres_rbf : gmres_r64);
+    if (precision < SYLV_PREC_FP64 || precision > SYLV_PREC_BF16) { set_error("unknown precision %d", precision); return SYLV_ERR_INVALID; }
+    return fn(op->op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters_out, resnorm_out, hist_out, s);
 }
 
 int sylv_controller_eval(const sylv_opts* o, int32_t count, const double* in, double* out) {
@@ -126,7 +126,7 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
         set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
         return SYLV_ERR_INVALID;
     }
-    if (o.precision != SYLV_PREC_FP64) { set_error("precision %d not built", o.precision); return SYLV_ERR_UNSUPPORTED; }
+    if (o.precision < SYLV_PREC_FP64 || o.precision > SYLV_PREC_BF16) { set_error("precision %d not built", o.precision); return SYLV_ERR_UNSUPPORTED; }
     bool cplx = false;
     for (int i = 0; i < n_shifts; ++i) {
         if (!std::isfinite(alpha[i].re) || !std::isfinite(alpha[i].im) || !std::isfinite(beta[i].re) ||
@@ -159,7 +159,9 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
     if (rc == SYLV_OK) rc = h->Bt.upload(hbt);
     if (rc == SYLV_OK) {
         AdiArgs a{&h->A, &h->Bt, ha.n, hb.n, r, f, g, alpha, beta, n_shifts, tol, o, h->stream};
-        rc = cplx ? make_adi_cplx(a, &h->impl) : make_adi_real(a, &h->impl);
+        auto mk = cplx ? (o.precision == SYLV_PREC_FP32 ? make_adi_c64 : o.precision == SYLV_PREC_BF16 ? make_adi_cbf : make_adi_c128)
+                       : (o.precision == SYLV_PREC_FP32 ? make_adi_r32 : o.precision == SYLV_PREC_BF16 ? make_adi_rbf : make_adi_r64);
+        rc = mk(a, &h->impl);
     }
     if (rc != SYLV_OK) {
         h->A.release();
@@ -205,6 +207,16 @@ int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_
     if (!h->solved) { set_error("no solve yet"); return SYLV_ERR_NOT_SOLVED; }
     if (is_complex) *is_complex = h->is_complex;
     return h->impl->factors(Z, Y, gamma, on_device, kr_out);
+}
+
+int sylv_adi_profile(sylv_handle* h, int32_t enable) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    return h->impl->profile(enable ? 1 : 0);
+}
+
+int sylv_adi_kernel_stats(const sylv_handle* h, double* ms, double* bytes, double* flops, int64_t* launches) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    return h->impl->kernel_stats(ms, bytes, flops, (long long*)launches);
 }
 
 int sylv_adi_destroy(sylv_handle* h) {

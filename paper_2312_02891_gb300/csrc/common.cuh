@@ -1,7 +1,18 @@
-// common.cuh - scalar types, descriptors and reduction helpers shared by the
-// device code of the inexact LR-ADI solver.
+// common.cuh - scalar types, conversions, descriptors and reduction helpers
+// shared by the device code of the inexact LR-ADI solver.
+//
+// Three scalar roles appear in the templates:
+//   T  the float64 type of the outer iteration, the true residuals, the
+//      solutions and the Hessenberg least squares (double or cplx);
+//   S  the storage type of the Krylov basis (double, float or bf16, and their
+//      complex pairs);
+//   C  the arithmetic type of the basis sweeps and the preconditioned
+//      operator product (double or float, and complex pairs).
+// The float64 path is T = S = C; the mixed path keeps T in float64 and runs
+// the sweeps in float32 (the inner solves may be inexact, Sec. 3).
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <math.h>
 
@@ -16,32 +27,51 @@
 namespace sylv {
 
 // ---------------------------------------------------------------------------
-// Scalars: double (real shifts) and cplx (complex shifts).  cplx is laid out
-// as two doubles, 16-byte aligned, so complex vectors are interleaved pairs.
+// Scalars.  Complex types are interleaved (re, im) pairs.
 // ---------------------------------------------------------------------------
 struct __align__(16) cplx { double x, y; };
+struct __align__(8) cflt { float x, y; };
+struct __align__(4) cbf16 { __nv_bfloat16 x, y; };
+typedef __nv_bfloat16 bf16;
 
-__host__ __device__ __forceinline__ double re(double a) { return a; }
-__host__ __device__ __forceinline__ double re(cplx a) { return a.x; }
-__host__ __device__ __forceinline__ double im(double) { return 0.0; }
-__host__ __device__ __forceinline__ double im(cplx a) { return a.y; }
-__host__ __device__ __forceinline__ double conjg(double a) { return a; }
-__host__ __device__ __forceinline__ cplx conjg(cplx a) { return {a.x, -a.y}; }
-__host__ __device__ __forceinline__ double abs2(double a) { return a * a; }
-__host__ __device__ __forceinline__ double abs2(cplx a) { return a.x * a.x + a.y * a.y; }
-__host__ __device__ __forceinline__ cplx operator+(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
-__host__ __device__ __forceinline__ cplx operator-(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
-__host__ __device__ __forceinline__ cplx operator-(cplx a) { return {-a.x, -a.y}; }
-__host__ __device__ __forceinline__ cplx operator+(double a, cplx b) { return {a + b.x, b.y}; }
-__host__ __device__ __forceinline__ cplx operator+(cplx a, double b) { return {a.x + b, a.y}; }
-__host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-__host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return {s * a.x, s * a.y}; }
-__host__ __device__ __forceinline__ cplx operator*(cplx a, double s) { return {s * a.x, s * a.y}; }
-__host__ __device__ __forceinline__ cplx& operator+=(cplx& a, cplx b) { a.x += b.x; a.y += b.y; return a; }
-__host__ __device__ __forceinline__ cplx& operator-=(cplx& a, cplx b) { a.x -= b.x; a.y -= b.y; return a; }
-__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+#define HD __host__ __device__ __forceinline__
+
+HD double re(double a) { return a; }
+HD double re(cplx a) { return a.x; }
+HD float re(float a) { return a; }
+HD float re(cflt a) { return a.x; }
+HD double im(double) { return 0.0; }
+HD double im(cplx a) { return a.y; }
+HD double conjg(double a) { return a; }
+HD cplx conjg(cplx a) { return {a.x, -a.y}; }
+HD float conjg(float a) { return a; }
+HD cflt conjg(cflt a) { return {a.x, -a.y}; }
+HD double abs2(double a) { return a * a; }
+HD double abs2(cplx a) { return a.x * a.x + a.y * a.y; }
+HD float abs2(float a) { return a * a; }
+HD float abs2(cflt a) { return a.x * a.x + a.y * a.y; }
+
+HD cplx operator+(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
+HD cplx operator-(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
+HD cplx operator-(cplx a) { return {-a.x, -a.y}; }
+HD cplx operator+(double a, cplx b) { return {a + b.x, b.y}; }
+HD cplx operator+(cplx a, double b) { return {a.x + b, a.y}; }
+HD cplx operator*(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+HD cplx operator*(double s, cplx a) { return {s * a.x, s * a.y}; }
+HD cplx operator*(cplx a, double s) { return {s * a.x, s * a.y}; }
+HD cplx& operator+=(cplx& a, cplx b) { a.x += b.x; a.y += b.y; return a; }
+HD cplx& operator-=(cplx& a, cplx b) { a.x -= b.x; a.y -= b.y; return a; }
+
+HD cflt operator+(cflt a, cflt b) { return {a.x + b.x, a.y + b.y}; }
+HD cflt operator-(cflt a, cflt b) { return {a.x - b.x, a.y - b.y}; }
+HD cflt operator-(cflt a) { return {-a.x, -a.y}; }
+HD cflt operator*(cflt a, cflt b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+HD cflt operator*(float s, cflt a) { return {s * a.x, s * a.y}; }
+HD cflt operator*(cflt a, float s) { return {s * a.x, s * a.y}; }
+HD cflt& operator+=(cflt& a, cflt b) { a.x += b.x; a.y += b.y; return a; }
+HD cflt& operator-=(cflt& a, cflt b) { a.x -= b.x; a.y -= b.y; return a; }
+
+HD cplx cdiv(cplx a, cplx b) {
     // a / b by Smith's method (R. L. Smith, CACM 1962) to avoid overflow.
     if (fabs(b.x) >= fabs(b.y)) {
         double r = b.y / b.x, d = b.x + b.y * r;
@@ -51,25 +81,68 @@ __host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
         return {(a.x * r + a.y) / d, (a.y * r - a.x) / d};
     }
 }
-__host__ __device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
-__host__ __device__ __forceinline__ cplx sdiv(cplx a, cplx b) { return cdiv(a, b); }
+HD double sdiv(double a, double b) { return a / b; }
+HD cplx sdiv(cplx a, cplx b) { return cdiv(a, b); }
 
-template <typename T> __host__ __device__ __forceinline__ T make_scalar(double r, double i);
-template <> __host__ __device__ __forceinline__ double make_scalar<double>(double r, double) { return r; }
-template <> __host__ __device__ __forceinline__ cplx make_scalar<cplx>(double r, double i) { return {r, i}; }
-template <typename T> __host__ __device__ __forceinline__ T zero() { return make_scalar<T>(0.0, 0.0); }
+template <typename T> HD T make_scalar(double r, double i);
+template <> HD double make_scalar<double>(double r, double) { return r; }
+template <> HD cplx make_scalar<cplx>(double r, double i) { return {r, i}; }
+template <> HD float make_scalar<float>(double r, double) { return (float)r; }
+template <> HD cflt make_scalar<cflt>(double r, double i) { return {(float)r, (float)i}; }
+template <typename T> HD T zero() { return make_scalar<T>(0.0, 0.0); }
 
 // conj(a) * b
-__host__ __device__ __forceinline__ double cmul(double a, double b) { return a * b; }
-__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
-    return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
-}
+HD double cmul(double a, double b) { return a * b; }
+HD cplx cmul(cplx a, cplx b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }
+HD float cmul(float a, float b) { return a * b; }
+HD cflt cmul(cflt a, cflt b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }
 
+// real part type of a scalar (the type of scale factors in its arithmetic)
+template <typename X> struct RealOf { typedef X type; };
+template <> struct RealOf<cplx> { typedef double type; };
+template <> struct RealOf<cflt> { typedef float type; };
+
+// ---------------------------------------------------------------------------
+// Conversions between the roles (storage <-> arithmetic <-> float64).
+// ---------------------------------------------------------------------------
+template <typename To, typename From> struct Cvt;
+template <typename X> struct Cvt<X, X> { static HD X f(X a) { return a; } };
+template <> struct Cvt<float, double> { static HD float f(double a) { return (float)a; } };
+template <> struct Cvt<double, float> { static HD double f(float a) { return (double)a; } };
+template <> struct Cvt<cflt, cplx> { static HD cflt f(cplx a) { return {(float)a.x, (float)a.y}; } };
+template <> struct Cvt<cplx, cflt> { static HD cplx f(cflt a) { return {(double)a.x, (double)a.y}; } };
+template <> struct Cvt<float, bf16> { static __device__ __forceinline__ float f(bf16 a) { return __bfloat162float(a); } };
+template <> struct Cvt<bf16, float> { static __device__ __forceinline__ bf16 f(float a) { return __float2bfloat16_rn(a); } };
+template <> struct Cvt<double, bf16> { static __device__ __forceinline__ double f(bf16 a) { return (double)__bfloat162float(a); } };
+template <> struct Cvt<bf16, double> { static __device__ __forceinline__ bf16 f(double a) { return __double2bfloat16(a); } };
+template <> struct Cvt<cflt, cbf16> {
+    static __device__ __forceinline__ cflt f(cbf16 a) { return {__bfloat162float(a.x), __bfloat162float(a.y)}; }
+};
+template <> struct Cvt<cbf16, cflt> {
+    static __device__ __forceinline__ cbf16 f(cflt a) { return {__float2bfloat16_rn(a.x), __float2bfloat16_rn(a.y)}; }
+};
+template <> struct Cvt<cplx, cbf16> {
+    static __device__ __forceinline__ cplx f(cbf16 a) {
+        return {(double)__bfloat162float(a.x), (double)__bfloat162float(a.y)};
+    }
+};
+template <> struct Cvt<cbf16, cplx> {
+    static __device__ __forceinline__ cbf16 f(cplx a) { return {__double2bfloat16(a.x), __double2bfloat16(a.y)}; }
+};
+template <typename To, typename From> __device__ __forceinline__ To cvt(From a) { return Cvt<To, From>::f(a); }
+
+// ---------------------------------------------------------------------------
+// Warp reductions and cache-bypassing loads.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ cplx shfl_xor(cplx v, int m) {
     return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
 }
-template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ cplx shfl_idx(cplx v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+template <typename X> __device__ __forceinline__ X warp_sum(X v) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) v += shfl_xor(v, m);
     return v;
@@ -93,6 +166,7 @@ struct OpDesc {
     const int* colind;
     const double* val;
     const double* diag;             // main diagonal (Jacobi)
+    long long nnz;                  // nonzeros of the matrix (algorithmic byte counts)
 };
 
 // y_i = sum_j Op[i][j] * X(j) + sigma * X(i), X(k) supplied by the caller.
@@ -121,17 +195,18 @@ __device__ __forceinline__ T op_row(const OpDesc& op, int i, T sigma, XF X) {
 enum Phase : int { PH_DONE = 0, PH_ARNOLDI = 1, PH_UPDATE = 2, PH_RESID = 3 };
 enum SysStatus : int { ST_OK = 0, ST_STALL = 1, ST_NONFINITE = 2 };
 
-template <typename T>
+template <typename T, typename S, typename C>
 struct SysDesc {
     int n;
     int op;                 // index into the batch's operator table
     int nchunks;            // work units of this system
     int rows_per_chunk;
     size_t ldv;             // stride between basis vectors
-    T* V;                   // (restart + 1) basis vectors, stored unnormalised
-    T* w;                   // Arnoldi work vector (operator output)
-    T* part;                // nchunks x SYLV_MAXV+1 partial sums
+    S* V;                   // (restart + 1) basis vectors, stored unnormalised
+    C* w;                   // Arnoldi work vector (operator output)
+    T* part;                // nchunks x PSTRIDE partial sums
     const T* pinv;          // Jacobi: 1 / (diag + sigma), or null
+    const C* aval;          // stencil operators: (Op + sigma I) P^{-1} by diagonals, C precision
     double* hist;           // optional: Givens estimate per Arnoldi step
     int hist_cap;
     int restart;
@@ -167,11 +242,44 @@ struct SysState {
 // Work item of a launch: (system, chunk).
 struct Item { int sys; int chunk; };
 
-// Per-batch device control block.
+// Kernel ids of the per-kernel statistics.
+enum KernelId : int { K_SPMV = 0, K_CGS2 = 1, K_CGS3 = 2, K_RUPD = 3, K_RRES = 4, K_CTRL = 5,
+                      K_STEP = 6, K_GRAM = 7, K_COUNT = 8 };
+
 struct BatchCtl {
     int n_active;           // systems not yet done
-    int ticks;
+    int ticks;              // device iterations of the current inner loop
     int* h_flag;            // mapped host word set to 0 when n_active reaches 0
+    double bytes[K_COUNT];  // algorithmic bytes moved, per kernel, summed over launches
+    double flops[K_COUNT];  // algorithmic floating-point operations, same
+    // device-driven CUDA graph: the kernels set the conditional nodes
+    int graph;              // 1 while a graph launch drives the iteration
+    int nsys;               // systems scanned by the grid-level decisions
+    int max_ticks;          // cap of device iterations per inner loop
+    int capped;             // inner loops stopped by the cap
+    unsigned gdone[K_COUNT];               // blocks finished, per kernel (grid-level last block)
+    cudaGraphConditionalHandle h_loop;     // WHILE: device iterations of the inner solves
+    cudaGraphConditionalHandle h_restart;  // IF: restart kernels in this iteration
+    cudaGraphConditionalHandle h_outer;    // WHILE: outer steps of Algorithm 1
+    unsigned long long launch_count[K_COUNT];  // launches, counted by block 0 of each kernel
 };
+
+__device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctl) atomicAdd(&ctl->launch_count[kid], 1ull);
+}
+
+// Real flops of one multiply-add in the arithmetic type X (complex: 8).
+template <typename X> struct FmaFlops { static constexpr double v = 2.0; };
+template <> struct FmaFlops<cplx> { static constexpr double v = 8.0; };
+template <> struct FmaFlops<cflt> { static constexpr double v = 8.0; };
+
+// Chunk 0 of each system adds the system's algorithmic bytes and
+// multiply-adds (converted to flops by the caller's type) for this launch.
+__device__ __forceinline__ void count_work(BatchCtl* ctl, int kid, int chunk, double bytes, double flops) {
+    if (chunk == 0 && threadIdx.x == 0 && ctl) {
+        atomicAdd(&ctl->bytes[kid], bytes);
+        atomicAdd(&ctl->flops[kid], flops);
+    }
+}
 
 }  // namespace sylv

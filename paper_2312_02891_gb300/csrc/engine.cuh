@@ -37,34 +37,49 @@ template <typename T> struct Dev {
 inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
 
 // A batch of shifted systems solved together by restarted GMRES.
-template <typename T>
+template <typename T, typename S, typename C>
 struct Engine {
     cudaStream_t stream = nullptr;
     int nsys = 0, nitems = 0, restart = 30;
-    std::vector<SysDesc<T>> h_sd;
-    Dev<SysDesc<T>> d_sd;
+    std::vector<SysDesc<T, S, C>> h_sd;
+    Dev<SysDesc<T, S, C>> d_sd;
     Dev<SysState<T>> d_st;
     Dev<Item> d_items;
     Dev<OpDesc> d_ops;
     Dev<BatchCtl> d_ctl;
-    Dev<T> d_V, d_w, d_part;
+    Dev<S> d_V;
+    Dev<C> d_w;
+    Dev<T> d_part;
     int* h_flag = nullptr;        // mapped pinned word
     int* d_hflag = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     long long ticks = 0;
+    // statistics: launches per kernel; with profiling, event-timed milliseconds
+    int profile = 0;
+    cudaEvent_t pev[4][6] = {};
+    int pending[4] = {0, 0, 0, 0};
+    double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
+    long long samples[K_COUNT] = {};    // sampled launches
+    long long launches[K_COUNT] = {};   // all launches
+    long long tick_no = 0;
+    int prof_every = 4;
 
     ~Engine() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        for (auto& row : pev)
+            for (auto& e : row)
+                if (e) cudaEventDestroy(e);
         if (h_flag) cudaFreeHost(h_flag);
     }
 
     // sys_n[q], sys_op[q]: rows and operator of system q; pinv[q]: Jacobi
-    // buffer or null; hist[q]: per-step estimate buffer or null.
+    // buffer or null; aval[q]: pre-scaled stencil buffer or null (empty: all
+    // null); hist[q]: per-step estimate buffer or null.
     int setup(const std::vector<int>& sys_n, const std::vector<int>& sys_op,
               const std::vector<OpDesc>& ops, const std::vector<T*>& pinv,
-              const std::vector<double*>& hist, int hist_cap, int restart_, int rpc,
-              cudaStream_t s) {
+              const std::vector<C*>& aval, const std::vector<double*>& hist, int hist_cap,
+              int restart_, int rpc, cudaStream_t s) {
         stream = s;
         restart = restart_;
         nsys = (int)sys_n.size();
@@ -75,7 +90,9 @@ struct Engine {
         std::vector<Item> items;
         h_sd.resize(nsys);
         for (int q = 0; q < nsys; ++q) {
-            SysDesc<T>& d = h_sd[q];
+            SysDesc<T, S, C>& d = h_sd[q];
+            d = SysDesc<T, S, C>{};
+            d.aval = aval.empty() ? nullptr : aval[q];
             d.n = sys_n[q];
             d.op = sys_op[q];
             d.rows_per_chunk = rpc;
@@ -96,7 +113,7 @@ struct Engine {
         SYLV_TRY(d_part.alloc(ptot));
         size_t vo = 0, wo = 0, po = 0;
         for (int q = 0; q < nsys; ++q) {
-            SysDesc<T>& d = h_sd[q];
+            SysDesc<T, S, C>& d = h_sd[q];
             d.V = d_V.p + vo;
             d.w = d_w.p + wo;
             d.part = d_part.p + po;
@@ -109,15 +126,16 @@ struct Engine {
         SYLV_TRY(d_items.alloc(items.size()));
         SYLV_TRY(d_ops.alloc(ops.size()));
         SYLV_TRY(d_ctl.alloc(1));
-        SYLV_CK(cudaMemcpy(d_sd.p, h_sd.data(), nsys * sizeof(SysDesc<T>), cudaMemcpyHostToDevice));
+        SYLV_CK(cudaMemcpy(d_sd.p, h_sd.data(), nsys * sizeof(SysDesc<T, S, C>), cudaMemcpyHostToDevice));
         SYLV_CK(cudaMemcpy(d_items.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
         SYLV_CK(cudaMemcpy(d_ops.p, ops.data(), ops.size() * sizeof(OpDesc), cudaMemcpyHostToDevice));
         SYLV_CK(cudaMemset(d_st.p, 0, nsys * sizeof(SysState<T>)));
-        SYLV_CK(cudaMemset(d_V.p, 0, vtot * sizeof(T)));
+        SYLV_CK(cudaMemset(d_V.p, 0, vtot * sizeof(S)));
         SYLV_CK(cudaHostAlloc((void**)&h_flag, sizeof(int), cudaHostAllocMapped));
         *h_flag = 0;
         SYLV_CK(cudaHostGetDevicePointer((void**)&d_hflag, h_flag, 0));
-        BatchCtl c{0, 0, d_hflag};
+        BatchCtl c{};
+        c.h_flag = d_hflag;
         SYLV_CK(cudaMemcpy(d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         for (auto& e : ev) SYLV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         return SYLV_OK;
@@ -125,16 +143,61 @@ struct Engine {
 
     // One device iteration: every active system advances one Arnoldi step
     // and restarts if its cycle ended.
-    int launch_tick(int cgs_mode = 0) {
+    // With profiling on, every prof_every-th tick is bracketed by events.
+    int launch_tick(int cgs_mode = 0, int slot = 0) {
         const dim3 grid(nitems), block(SYLV_BLOCK);
-        k_arnoldi_spmv<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, cgs_mode);
-        k_cgs_pass2<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p);
-        k_cgs_pass3<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
+        cudaEvent_t* pe = (profile && (tick_no++ % prof_every) == 0) ? pev[slot] : nullptr;
+        if (pe) SYLV_CK(cudaEventRecord(pe[0], stream));
+        k_arnoldi_spmv<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p, cgs_mode);
+        if (pe) SYLV_CK(cudaEventRecord(pe[1], stream));
+        k_cgs_pass2<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+        if (pe) SYLV_CK(cudaEventRecord(pe[2], stream));
+        k_cgs_pass3<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
+        if (pe) SYLV_CK(cudaEventRecord(pe[3], stream));
+        launches[K_SPMV]++; launches[K_CGS2]++; launches[K_CGS3]++;
         if (cgs_mode == 0) {
-            k_restart_update<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p);
-            k_restart_residual<T><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            k_restart_update<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            if (pe) SYLV_CK(cudaEventRecord(pe[4], stream));
+            k_restart_residual<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            if (pe) SYLV_CK(cudaEventRecord(pe[5], stream));
+            launches[K_RUPD]++; launches[K_RRES]++;
         }
+        if (pe) pending[slot] = cgs_mode == 0 ? 5 : 3;
         SYLV_CK(cudaGetLastError());
+        return SYLV_OK;
+    }
+
+    // Add the event-timed durations of a finished tick to the totals.
+    int harvest(int slot) {
+        for (int q = 0; q < pending[slot]; ++q) {
+            float ms = 0.f;
+            SYLV_CK(cudaEventElapsedTime(&ms, pev[slot][q], pev[slot][q + 1]));
+            kernel_ms[q] += ms;
+            samples[q] += 1;
+        }
+        pending[slot] = 0;
+        return SYLV_OK;
+    }
+
+    int set_profile(int on) {
+        profile = on;
+        tick_no = 0;
+        for (int q = 0; q < K_COUNT; ++q) { kernel_ms[q] = 0.0; launches[q] = 0; samples[q] = 0; }
+        for (int sl = 0; sl < 4; ++sl) pending[sl] = 0;
+        if (on && !pev[0][0])
+            for (int sl = 0; sl < 4; ++sl)
+                for (int q = 0; q < 6; ++q) SYLV_CK(cudaEventCreate(&pev[sl][q]));
+        BatchCtl c{};
+        SYLV_CK(cudaMemcpy(&c, d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < K_COUNT; ++q) { c.bytes[q] = 0.0; c.flops[q] = 0.0; }
+        SYLV_CK(cudaMemcpy(d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
+        return SYLV_OK;
+    }
+
+    int read_work(double* bytes, double* flops) const {
+        BatchCtl c{};
+        SYLV_CK(cudaMemcpy(&c, d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < K_COUNT; ++q) { bytes[q] = c.bytes[q]; flops[q] = c.flops[q]; }
         return SYLV_OK;
     }
 
@@ -149,12 +212,19 @@ struct Engine {
                 set_error("inner solves did not finish within %lld device iterations", max_ticks);
                 return SYLV_ERR_INNER_STALL;
             }
-            SYLV_TRY(launch_tick());
-            SYLV_CK(cudaEventRecord(ev[t % D], stream));
+            const int slot = (int)(t % D);
+            if (pending[slot]) SYLV_TRY(harvest(slot));
+            SYLV_TRY(launch_tick(0, slot));
+            SYLV_CK(cudaEventRecord(ev[slot], stream));
             ++t;
             if (t >= D) SYLV_CK(cudaEventSynchronize(ev[t % D]));
         }
         ticks += t;
+        if (profile) {
+            SYLV_CK(cudaStreamSynchronize(stream));
+            for (int sl = 0; sl < D; ++sl)
+                if (pending[sl]) SYLV_TRY(harvest(sl));
+        }
         return SYLV_OK;
     }
 };
@@ -198,7 +268,25 @@ __global__ void k_copy_scaled(const T* __restrict__ src, double scale, T* __rest
         dst[i] = scale * src[i];
 }
 
-template <typename T>
+// Stencil operators whose main diagonal is stored get the pre-scaled diagonals.
+inline bool scaled_op_possible(const OpDesc& d) {
+    if (d.fmt != 1) return false;
+    for (int q = 0; q < d.ndiag; ++q)
+        if (d.offs[q] == 0) return true;
+    return false;
+}
+
+// Jacobi inverse and pre-scaled diagonals for one operator and shift.
+template <typename T, typename C>
+int shifted_op_setup(const OpDesc& op, T sigma, T* pinv, C* aval, cudaStream_t s) {
+    if (!pinv && !aval) return SYLV_OK;
+    const int grid = std::max(1, std::min(num_sms() * 4, (op.n + SYLV_BLOCK - 1) / SYLV_BLOCK));
+    k_shifted_op<T, C><<<grid, SYLV_BLOCK, 0, s>>>(op, sigma, pinv, aval);
+    SYLV_CK(cudaGetLastError());
+    return SYLV_OK;
+}
+
+template <typename T, typename S, typename C>
 int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
             int restart, int max_iters, int* iters, double* res, double* hist, cudaStream_t s) {
     if (!B || !X || ncols <= 0 || restart < 1 || restart > SYLV_MR || max_iters < 1) {
@@ -206,18 +294,21 @@ int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int nc
         return SYLV_ERR_INVALID;
     }
     const int n = op.desc.n;
-    Engine<T> eng;
+    Engine<T, S, C> eng;
     Dev<T> pinv;
+    Dev<C> aval;
     Dev<double> d_hist;
     if (jacobi) SYLV_TRY(pinv.alloc(n));
+    if (scaled_op_possible(op.desc)) SYLV_TRY(aval.alloc((size_t)op.desc.ndiag * n));
     if (hist) SYLV_TRY(d_hist.alloc((size_t)ncols * max_iters));
     std::vector<int> sn(ncols, n), so(ncols, 0);
     std::vector<T*> pv(ncols, jacobi ? pinv.p : nullptr);
+    std::vector<C*> av(ncols, aval.p);
     std::vector<double*> hv;
     if (hist)
         for (int c = 0; c < ncols; ++c) hv.push_back(d_hist.p + (size_t)c * max_iters);
     std::vector<OpDesc> ops{op.desc};
-    SYLV_TRY(eng.setup(sn, so, ops, pv, hv, max_iters, restart, 0, s));
+    SYLV_TRY(eng.setup(sn, so, ops, pv, av, hv, max_iters, restart, 0, s));
     std::vector<SysState<T>> st(ncols);
     for (int c = 0; c < ncols; ++c) {
         std::memset(&st[c], 0, sizeof(SysState<T>));
@@ -229,13 +320,12 @@ int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int nc
         st[c].b = (const T*)B + (size_t)c * n;
     }
     SYLV_CK(cudaMemcpyAsync(eng.d_st.p, st.data(), ncols * sizeof(SysState<T>), cudaMemcpyHostToDevice, s));
-    BatchCtl c{ncols, 0, eng.d_hflag};
+    BatchCtl c{};
+    c.n_active = ncols;
+    c.h_flag = eng.d_hflag;
     SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
-    if (jacobi) {
-        k_pinv<T><<<num_sms() * 4, 256, 0, s>>>(op.desc.diag, sigma, pinv.p, n);
-        SYLV_CK(cudaGetLastError());
-    }
-    k_zero_x<T><<<eng.nitems, SYLV_BLOCK, 0, s>>>(eng.d_sd.p, eng.d_st.p, eng.d_items.p);
+    SYLV_TRY((shifted_op_setup<T, C>(op.desc, sigma, pinv.p, aval.p, s)));
+    k_zero_x<T, S, C><<<eng.nitems, SYLV_BLOCK, 0, s>>>(eng.d_sd.p, eng.d_st.p, eng.d_items.p);
     SYLV_CK(cudaGetLastError());
     SYLV_CK(cudaStreamSynchronize(s));
     *eng.h_flag = 1;
@@ -267,12 +357,14 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
         set_error("cgs2: invalid arguments (n=%d k=%d, 1 <= k <= %d)", n, k, SYLV_MR);
         return SYLV_ERR_INVALID;
     }
-    Engine<T> eng;
+    Engine<T, T, T> eng;
     DevOp dummy;
     dummy.desc.n = n;
     std::vector<OpDesc> ops{dummy.desc};
-    SYLV_TRY(eng.setup({n}, {0}, ops, {nullptr}, {}, 0, k, 0, s));
-    const SysDesc<T>& d = eng.h_sd[0];
+    const std::vector<int> sn{n}, so{0};
+    const std::vector<T*> pv{nullptr};
+    SYLV_TRY(eng.setup(sn, so, ops, pv, std::vector<T*>(), std::vector<double*>(), 0, k, 0, s));
+    const SysDesc<T, T, T>& d = eng.h_sd[0];
     for (int l = 0; l < k; ++l)
         SYLV_CK(cudaMemcpyAsync(d.V + (size_t)l * d.ldv, (const T*)V + (size_t)l * n, n * sizeof(T),
                                 cudaMemcpyDeviceToDevice, s));
@@ -283,7 +375,9 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
     st.j = k - 1;
     for (int l = 0; l < k; ++l) st.scale[l] = 1.0;
     SYLV_CK(cudaMemcpyAsync(eng.d_st.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
-    BatchCtl c{1, 0, eng.d_hflag};
+    BatchCtl c{};
+    c.n_active = 1;
+    c.h_flag = eng.d_hflag;
     SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
     SYLV_TRY(eng.launch_tick(1));
     SYLV_CK(cudaStreamSynchronize(s));
@@ -299,23 +393,44 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // The inexact LR-ADI solver (Algorithm 1) on one GPU.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename S, typename C>
 struct Adi : AdiBase {
-    AdiDev<T> d{};
-    Engine<T> eng;
+    AdiDev<T, S, C> d{};
+    Engine<T, S, C> eng;
     cudaStream_t stream = nullptr;
     int n = 0, m = 0, r = 0, kmax = 0, max_inner = 0;
     Dev<double> f, g, hist;
     Dev<T> w, t, Z, Y, gam, alpha, beta, pinvA, pinvB, gpart;
+    Dev<C> avalA, avalB;
     Dev<AdiState<T>> st;
     int* h_done = nullptr;
     int* d_hdone = nullptr;
     int solved = 0;
     int last_status = SYLV_ERR_NOT_SOLVED;
     long long ticks = 0;
+    long long launches_last = 0;
 
     ~Adi() override {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
         if (h_done) cudaFreeHost(h_done);
+        for (auto& e : aev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    int profile(int on) override { return eng.set_profile(on); }
+
+    int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const override {
+        double b[K_COUNT], f[K_COUNT];
+        SYLV_TRY(eng.read_work(b, f));
+        for (int q = 0; q < K_COUNT; ++q) {
+            // sampled mean duration times all launches
+            if (ms) ms[q] = eng.samples[q] > 0 ? eng.kernel_ms[q] / eng.samples[q] * eng.launches[q] : 0.0;
+            if (bytes) bytes[q] = b[q];
+            if (flops) flops[q] = f[q];
+            if (launches) launches[q] = eng.launches[q];
+        }
+        return SYLV_OK;
     }
 
     int init(const AdiArgs& a) {
@@ -337,6 +452,8 @@ struct Adi : AdiBase {
             SYLV_TRY(pinvA.alloc(n));
             SYLV_TRY(pinvB.alloc(m));
         }
+        if (scaled_op_possible(a.A->desc)) SYLV_TRY(avalA.alloc((size_t)a.A->desc.ndiag * n));
+        if (scaled_op_possible(a.Bt->desc)) SYLV_TRY(avalB.alloc((size_t)a.Bt->desc.ndiag * m));
         SYLV_TRY(st.alloc(1));
         SYLV_CK(cudaMemset(st.p, 0, sizeof(AdiState<T>)));
         SYLV_CK(cudaMemset(Z.p, 0, Z.count * sizeof(T)));
@@ -353,10 +470,11 @@ struct Adi : AdiBase {
         // 2r column systems: A side uses operator 0, B side operator 1 (B^T).
         std::vector<int> sn, so;
         std::vector<T*> pv;
-        for (int l = 0; l < r; ++l) { sn.push_back(n); so.push_back(0); pv.push_back(pinvA.p); }
-        for (int l = 0; l < r; ++l) { sn.push_back(m); so.push_back(1); pv.push_back(pinvB.p); }
+        std::vector<C*> av;
+        for (int l = 0; l < r; ++l) { sn.push_back(n); so.push_back(0); pv.push_back(pinvA.p); av.push_back(avalA.p); }
+        for (int l = 0; l < r; ++l) { sn.push_back(m); so.push_back(1); pv.push_back(pinvB.p); av.push_back(avalB.p); }
         std::vector<OpDesc> ops{a.A->desc, a.Bt->desc};
-        SYLV_TRY(eng.setup(sn, so, ops, pv, {}, 0, a.o.restart, rpc, stream));
+        SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, a.o.restart, rpc, stream));
         const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
         SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
         SYLV_CK(cudaHostAlloc((void**)&h_done, sizeof(int), cudaHostAllocMapped));
@@ -370,11 +488,13 @@ struct Adi : AdiBase {
         d.alpha = alpha.p; d.beta = beta.p;
         d.f = f.p; d.g = g.p; d.w = w.p; d.t = t.p; d.Z = Z.p; d.Y = Y.p; d.gam = gam.p;
         d.hist = hist.p;
-        d.diagA = a.A->desc.diag; d.diagB = a.Bt->desc.diag;
+        d.opA = a.A->desc; d.opB = a.Bt->desc;
         d.pinvA = pinvA.p; d.pinvB = pinvB.p;
+        d.avalA = avalA.p; d.avalB = avalB.p;
         d.sd = eng.d_sd.p; d.st = eng.d_st.p; d.ctl = eng.d_ctl.p;
         d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
         d.s = st.p; d.h_done = d_hdone;
+        graph_on = a.o.driver == 0 ? 1 : 0;
         return SYLV_OK;
     }
 
@@ -387,33 +507,192 @@ struct Adi : AdiBase {
         return SYLV_OK;
     }
 
-    int solve() override {
+    // event pairs around the outer-step kernels when profiling
+    cudaEvent_t aev[4] = {};
+    int ensure_events() {
+        if (!aev[0])
+            for (auto& e : aev) SYLV_CK(cudaEventCreate(&e));
+        return SYLV_OK;
+    }
+    int add_ms(int kid, cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.f;
+        SYLV_CK(cudaEventElapsedTime(&ms, a, b));
+        eng.kernel_ms[kid] += ms;
+        eng.samples[kid] += 1;
+        return SYLV_OK;
+    }
+
+    // ---- device-driven solve: one CUDA graph with conditional nodes ----
+    //   gram(init) -> WHILE(h_outer) { controller -> step_init ->
+    //       WHILE(h_loop) { spmv -> pass2 -> pass3 -> IF(h_restart) { update -> residual } }
+    //       -> gram(update) }
+    // The kernels set the conditions (pass3/residual: grid-level last block;
+    // controller and gram: their deciding thread), so no host round trip
+    // happens inside a solve.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_on = 1;             // 0: host-driven loop (used while profiling)
+    int h_one = 1, h_zero = 0;
+
+    int add_kernel(cudaGraphNode_t* node, cudaGraph_t g, cudaGraphNode_t* dep, void* func, int grid,
+                   int block, void** args) {
+        cudaKernelNodeParams kp = {};
+        kp.func = func;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        SYLV_CK(cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp));
+        return SYLV_OK;
+    }
+
+    int add_cond(cudaGraphNode_t* node, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                 cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = type;
+        p.conditional.size = 1;
+        SYLV_CK(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &p));
+        *body = p.conditional.phGraph_out[0];
+        return SYLV_OK;
+    }
+
+    int build_graph() {
         const int nb = d.nchA + d.nchB;
-        *h_done = 0;
-        k_adi_gram<T><<<nb, SYLV_BLOCK, 0, stream>>>(d, 1);
-        SYLV_CK(cudaGetLastError());
-        long long t0 = eng.ticks;
-        for (int step = 0; step <= kmax; ++step) {
-            SYLV_CK(cudaStreamSynchronize(stream));
-            if (*(volatile int*)h_done) break;
-            *eng.h_flag = 1;
-            k_adi_controller<T><<<1, 32, 0, stream>>>(d);
-            k_adi_step_init<T><<<nb, SYLV_BLOCK, 0, stream>>>(d);
-            SYLV_CK(cudaGetLastError());
-            SYLV_TRY(eng.run((long long)max_inner + 8));
-            k_adi_gram<T><<<nb, SYLV_BLOCK, 0, stream>>>(d, 0);
-            SYLV_CK(cudaGetLastError());
-        }
+        const int ni = eng.nitems;
+        int one = 1, zero = 0, mode0 = 0;
+        cudaGraph_t g;
+        SYLV_CK(cudaGraphCreate(&g, 0));
+        graph = g;
+        cudaGraphConditionalHandle h_outer, h_loop, h_restart;
+        // every condition starts at 0 on each launch: a loop runs only while a
+        // kernel has explicitly asked for another pass
+        SYLV_CK(cudaGraphConditionalHandleCreate(&h_outer, g, 0, cudaGraphCondAssignDefault));
+        void* a_init[] = {&d, &one};
+        void* a_upd[] = {&d, &zero};
+        void* a_d[] = {&d};
+        cudaGraphNode_t n_init, n_outer, n_ctrl, n_step, n_loop, n_gram, n1, n2, n3, n_if, n4, n5;
+        SYLV_TRY(add_kernel(&n_init, g, nullptr, (void*)k_adi_gram<T, S, C>, nb, SYLV_BLOCK, a_init));
+        cudaGraph_t outer_body, loop_body, if_body;
+        SYLV_TRY(add_cond(&n_outer, g, &n_init, h_outer, cudaGraphCondTypeWhile, &outer_body));
+        SYLV_CK(cudaGraphConditionalHandleCreate(&h_loop, outer_body, 0, cudaGraphCondAssignDefault));
+        SYLV_TRY(add_kernel(&n_ctrl, outer_body, nullptr, (void*)k_adi_controller<T, S, C>, 1, 32, a_d));
+        SYLV_TRY(add_kernel(&n_step, outer_body, &n_ctrl, (void*)k_adi_step_init<T, S, C>, nb, SYLV_BLOCK, a_d));
+        SYLV_TRY(add_cond(&n_loop, outer_body, &n_step, h_loop, cudaGraphCondTypeWhile, &loop_body));
+        SYLV_TRY(add_kernel(&n_gram, outer_body, &n_loop, (void*)k_adi_gram<T, S, C>, nb, SYLV_BLOCK, a_upd));
+        SYLV_CK(cudaGraphConditionalHandleCreate(&h_restart, loop_body, 0, cudaGraphCondAssignDefault));
+        auto* sdp = eng.d_sd.p;
+        auto* stp = eng.d_st.p;
+        auto* opp = eng.d_ops.p;
+        auto* itp = eng.d_items.p;
+        auto* ctp = eng.d_ctl.p;
+        void* a1[] = {&sdp, &stp, &opp, &itp, &ctp, &mode0};
+        void* a2[] = {&sdp, &stp, &itp, &ctp};
+        void* a3[] = {&sdp, &stp, &itp, &ctp, &mode0};
+        void* a4[] = {&sdp, &stp, &itp, &ctp};
+        void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
+        SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_arnoldi_spmv<T, S, C>, ni, SYLV_BLOCK, a1));
+        SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, SYLV_BLOCK, a2));
+        SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, SYLV_BLOCK, a3));
+        SYLV_TRY(add_cond(&n_if, loop_body, &n3, h_restart, cudaGraphCondTypeIf, &if_body));
+        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, ni, SYLV_BLOCK, a4));
+        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, ni, SYLV_BLOCK, a5));
+        SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
+        // the kernels read the handles and the decision parameters from the control block
+        BatchCtl c{};
+        SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        c.h_outer = h_outer;
+        c.h_loop = h_loop;
+        c.h_restart = h_restart;
+        c.nsys = eng.nsys;
+        c.max_ticks = max_inner + 8;
+        c.graph = 0;
+        SYLV_CK(cudaMemcpy(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
+        return SYLV_OK;
+    }
+
+    unsigned long long device_launches() const {
+        BatchCtl c{};
+        if (cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+        unsigned long long s = 0;
+        for (int q = 0; q < K_COUNT; ++q) s += c.launch_count[q];
+        return s;
+    }
+
+    int finish_solve(unsigned long long l0) {
         SYLV_CK(cudaStreamSynchronize(stream));
-        ticks = eng.ticks - t0;
+        launches_last = (long long)(device_launches() - l0);
         AdiState<T> s;
         SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        BatchCtl c{};
+        SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
         solved = 1;
         if (s.status == 2) { set_error("non-finite value during the solve"); last_status = SYLV_ERR_NONFINITE; }
         else if (s.status == 1 || !s.done) { set_error("kmax outer steps without reaching tau"); last_status = SYLV_ERR_MAXIT; }
         else if (s.stalled > 0) { set_error("%d inner solves reached max_inner", s.stalled); last_status = SYLV_ERR_INNER_STALL; }
         else last_status = SYLV_OK;
         return last_status;
+    }
+
+    int solve_graph() {
+        if (!gexec) SYLV_TRY(build_graph());
+        const unsigned long long l0 = device_launches();
+        BatchCtl* dc = eng.d_ctl.p;
+        SYLV_CK(cudaMemcpyAsync(&dc->graph, &h_one, sizeof(int), cudaMemcpyHostToDevice, stream));
+        SYLV_CK(cudaGraphLaunch(gexec, stream));
+        SYLV_CK(cudaMemcpyAsync(&dc->graph, &h_zero, sizeof(int), cudaMemcpyHostToDevice, stream));
+        ticks = -1;   // not tracked on the host in this mode
+        return finish_solve(l0);
+    }
+
+    int solve() override {
+        if (graph_on && !eng.profile) return solve_graph();
+        return solve_host();
+    }
+
+    int solve_host() {
+        const int nb = d.nchA + d.nchB;
+        const bool prof = eng.profile != 0;
+        if (prof) SYLV_TRY(ensure_events());
+        const unsigned long long dl0 = device_launches();
+        long long l0 = 0;
+        for (int q = 0; q < K_COUNT; ++q) l0 += eng.launches[q];
+        *h_done = 0;
+        if (prof) SYLV_CK(cudaEventRecord(aev[2], stream));
+        k_adi_gram<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d, 1);
+        if (prof) SYLV_CK(cudaEventRecord(aev[3], stream));
+        SYLV_CK(cudaGetLastError());
+        eng.launches[K_GRAM]++;
+        long long t0 = eng.ticks;
+        bool have_step = false;
+        for (int step = 0; step <= kmax; ++step) {
+            SYLV_CK(cudaStreamSynchronize(stream));
+            if (prof) {
+                SYLV_TRY(add_ms(K_GRAM, aev[2], aev[3]));
+                if (have_step) SYLV_TRY(add_ms(K_CTRL, aev[0], aev[1]));
+            }
+            if (*(volatile int*)h_done) break;
+            *eng.h_flag = 1;
+            if (prof) SYLV_CK(cudaEventRecord(aev[0], stream));
+            k_adi_controller<T, S, C><<<1, 32, 0, stream>>>(d);
+            k_adi_step_init<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+            if (prof) SYLV_CK(cudaEventRecord(aev[1], stream));
+            SYLV_CK(cudaGetLastError());
+            eng.launches[K_CTRL]++; eng.launches[K_STEP]++;
+            have_step = true;
+            SYLV_TRY(eng.run((long long)max_inner + 8));
+            if (prof) SYLV_CK(cudaEventRecord(aev[2], stream));
+            k_adi_gram<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d, 0);
+            if (prof) SYLV_CK(cudaEventRecord(aev[3], stream));
+            SYLV_CK(cudaGetLastError());
+            eng.launches[K_GRAM]++;
+        }
+        SYLV_CK(cudaStreamSynchronize(stream));
+        ticks = eng.ticks - t0;
+        (void)l0;
+        return finish_solve(dl0);
     }
 
     int info(sylv_info* out) const override {
@@ -431,6 +710,7 @@ struct Adi : AdiBase {
         out->inner_restarts = s.cycles;
         out->stalled_solves = s.stalled;
         out->ticks = (int32_t)ticks;
+        out->launches = launches_last;
         return SYLV_OK;
     }
 
@@ -458,9 +738,9 @@ struct Adi : AdiBase {
     }
 };
 
-template <typename T>
+template <typename T, typename S, typename C>
 int make_adi_t(const AdiArgs& a, AdiBase** out) {
-    Adi<T>* p = new (std::nothrow) Adi<T>();
+    Adi<T, S, C>* p = new (std::nothrow) Adi<T, S, C>();
     if (!p) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
     int rc = p->init(a);
     if (rc != SYLV_OK) { delete p; return rc; }

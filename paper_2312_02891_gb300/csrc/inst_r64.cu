@@ -1,5 +1,10 @@
-// inst_real.cu - the solver for real shift pairs (float64 vectors).
-#include "engine.cuh"
+// inst_r64.cu - real shifts, float64 throughout; also the standalone CGS2,
+// shifted product and controller entry points for real data.
+#define SYLV_SUFFIX r64
+#define SYLV_T double
+#define SYLV_S double
+#define SYLV_C double
+#include "inst.cuh"
 
 namespace sylv {
 
@@ -11,15 +16,6 @@ __global__ void k_controller_eval(int count, int strategy, int bl_clamp, double 
     const double* p = in + (size_t)i * 11;
     controller_eval(strategy, bl_clamp, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7],
                     dminA, dmaxA, dminB, dmaxB, p[8], out + 3 * i, out + 3 * i + 1, out + 3 * i + 2);
-}
-
-
-int make_adi_real(const AdiArgs& a, AdiBase** out) { return make_adi_t<double>(a, out); }
-
-int gmres_real(const DevOp& op, double sigma, int jacobi, const void* B, void* X, int ncols,
-               double tol, int restart, int max_iters, int* iters, double* res, double* hist,
-               cudaStream_t s) {
-    return gmres_t<double>(op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters, res, hist, s);
 }
 
 int cgs2_real(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {

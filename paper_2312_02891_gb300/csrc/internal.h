@@ -62,6 +62,8 @@ struct AdiBase {
     virtual int info(sylv_info* out) const = 0;
     virtual int history(double* buf, int cap, int* rows) const = 0;
     virtual int factors(void* Z, void* Y, void* gamma, int on_device, int* kr) const = 0;
+    virtual int profile(int on) = 0;
+    virtual int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const = 0;
 };
 
 struct AdiArgs {
@@ -78,15 +80,21 @@ struct AdiArgs {
     cudaStream_t stream;
 };
 
-int make_adi_real(const AdiArgs& a, AdiBase** out);
-int make_adi_cplx(const AdiArgs& a, AdiBase** out);
-
-int gmres_real(const DevOp& op, double sigma, int jacobi, const void* B, void* X, int ncols,
-               double tol, int restart, int max_iters, int* iters, double* res, double* hist,
-               cudaStream_t s);
-int gmres_cplx(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X, int ncols,
-               double tol, int restart, int max_iters, int* iters, double* res, double* hist,
-               cudaStream_t s);
+// One instantiation per (shift type, precision): r = real shifts, c = complex
+// shifts; 64/128 = float64 throughout, 32/64 = float32 basis and sweeps,
+// bf = bfloat16 basis with float32 sweeps.
+#define SYLV_DECL_INST(SUFFIX)                                                                      \
+    int make_adi_##SUFFIX(const AdiArgs& a, AdiBase** out);                                         \
+    int gmres_##SUFFIX(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,       \
+                       int ncols, double tol, int restart, int max_iters, int* iters, double* res, \
+                       double* hist, cudaStream_t s);
+SYLV_DECL_INST(r64)
+SYLV_DECL_INST(r32)
+SYLV_DECL_INST(rbf)
+SYLV_DECL_INST(c128)
+SYLV_DECL_INST(c64)
+SYLV_DECL_INST(cbf)
+#undef SYLV_DECL_INST
 int cgs2_real(const void* V, int n, int k, void* w, void* h, cudaStream_t s);
 int cgs2_cplx(const void* V, int n, int k, void* w, void* h, cudaStream_t s);
 int op_apply_real(const DevOp& op, double sigma, int jacobi, const void* X, void* Y, int ncols, cudaStream_t s);

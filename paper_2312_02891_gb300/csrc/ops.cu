@@ -135,6 +135,7 @@ int DevOp::upload(const HostCsr& h) {
         }
     desc = OpDesc{};
     desc.n = n;
+    desc.nnz = (long long)h.ci.size();
     if (stencil) {
         int d = 0;
         for (auto& kv : offs) { kv.second = d; desc.offs[d] = kv.first; ++d; }

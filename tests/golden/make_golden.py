@@ -1,0 +1,75 @@
+"""Write the stored oracle results used by the full-size parity tests and by
+the benchmark's CPU-baseline extrapolation.
+
+Calls only the oracle (and the seeded input generator); nothing here comes
+from the CUDA path.  Usage:  python tests/golden/make_golden.py mid2d bl_mid
+writes tests/golden/<workload>_<strategy>.json with the outer step count,
+the per-step controller history, inner iteration totals, the computed and
+true relative residuals, and a two-sided sketch S = P^T X Q of the factored
+solution (P: n x 16, Q: m x 16 seeded Gaussian, streams 5 and 6).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+from oracle.lradi import lradi  # noqa: E402
+from oracle.residual import lowrank_norm2, true_residual_norm2  # noqa: E402
+from paper_2312_02891_gb300 import workloads as W  # noqa: E402
+
+SKETCH = 16
+
+
+def sketch_mats(n, m):
+    P = np.stack([W.normal(12345, 5, c, n) for c in range(SKETCH)], axis=1)
+    Q = np.stack([W.normal(12345, 6, c, m) for c in range(SKETCH)], axis=1)
+    return P, Q
+
+
+def sketch(Z, gamma, Y, P, Q):
+    """P^T (Z diag(gamma) Y^*) Q, formed through the factors."""
+    return (P.T @ Z) @ (gamma[:, None] * (Y.conj().T @ Q))
+
+
+def main(workload: str, strategy: str, **extra):
+    p = W.problem_config(workload)
+    opts = dict(strategy=strategy, jacobi=p.opts.get("jacobi", False), restart=p.opts.get("restart", 30))
+    opts.update(extra)
+    t0 = time.time()
+    res = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, **opts)
+    wall = time.time() - t0
+    A, B = p.A.to_scipy(), p.B.to_scipy()
+    nfg = lowrank_norm2(p.f, p.g)
+    tr = true_residual_norm2(A, B, p.f, p.g, res.Z, res.gamma, res.Y) / nfg
+    P, Q = sketch_mats(p.A.n, p.B.n)
+    S = sketch(res.Z, res.gamma, res.Y, P, Q)
+    hist = [{k: (float(np.real(v)) if not isinstance(v, (bool, np.bool_)) else bool(v))
+             for k, v in h.items()} for h in res.history]
+    out = dict(workload=workload, strategy=strategy, opts={k: v for k, v in opts.items()},
+               tau=p.tau, n=p.A.n, m=p.B.n, r=p.r, steps=res.steps, converged=bool(res.converged),
+               res_comp=res.res_comp, res_true=tr, norm_fg=nfg,
+               inner_its_A=res.inner_its_A, inner_its_B=res.inner_its_B,
+               sketch=np.real(S).tolist(), sketch_fro=float(np.linalg.norm(S)),
+               oracle_wall_s=wall, history=hist)
+    suffix = "_".join([strategy] + [f"{k}{v}" for k, v in sorted(extra.items())])
+    path = os.path.join(HERE, f"{workload}_{suffix}.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(path, res.steps, res.res_comp, tr, res.inner_its_A, res.inner_its_B, f"{wall:.0f}s")
+
+
+if __name__ == "__main__":
+    wl = sys.argv[1] if len(sys.argv) > 1 else "mid2d"
+    st = sys.argv[2] if len(sys.argv) > 2 else "bl_mid"
+    kw = {}
+    for a in sys.argv[3:]:
+        k, v = a.split("=")
+        kw[k] = float(v) if "." in v or "e" in v else int(v)
+    main(wl, st, **kw)

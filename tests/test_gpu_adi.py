@@ -51,15 +51,24 @@ def compare(p, strategy, jacobi, xtol=1e-6, **extra):
     # factored solutions agree
     dX = factored_diff_fro(Z, gam, Y, ref.Z, ref.gamma, ref.Y) / factored_fro(ref.Z, ref.gamma, ref.Y)
     assert dX <= xtol, dX
-    # step-by-step history over the common steps: shifts, tolerances, residuals
+    # step-by-step history over the common steps: shifts, tolerances, residuals.
+    # Mixed precision changes the inner solutions within their tolerances, so
+    # the norms of w_k agree to that level rather than to rounding.
+    mixed = extra.get("precision", "fp64") != "fp64"
     ks = min(len(hist), len(ref.history))
     for i in range(ks):
         h, o = hist[i], ref.history[i]
         assert h[0] == o["k"]
         assert h[1] == pytest.approx(np.real(o["alpha"])) and h[2] == pytest.approx(np.real(o["beta"]))
-        assert h[3] == pytest.approx(o["dA"], rel=1e-3) and h[4] == pytest.approx(o["dB"], rel=1e-3)
-        assert h[12] == pytest.approx(o["res_comp"], rel=1e-3, abs=1e-3 * p.tau)
-        assert h[13] == pytest.approx(o["N_w"], rel=1e-6)
+        if not mixed:
+            assert h[3] == pytest.approx(o["dA"], rel=1e-3) and h[4] == pytest.approx(o["dB"], rel=1e-3)
+        elif not strategy.startswith("bl_"):
+            # without back-looking the tolerances depend only on ||w||, ||t||
+            assert h[3] == pytest.approx(o["dA"], rel=0.05) and h[4] == pytest.approx(o["dB"], rel=0.05)
+        # (back-looking tolerances follow the achieved inner residuals, which
+        # float32 inner solves change within their tolerances)
+        assert h[12] == pytest.approx(o["res_comp"], rel=0.05 if mixed else 1e-3, abs=1e-3 * p.tau)
+        assert h[13] == pytest.approx(o["N_w"], rel=1e-3 if mixed else 1e-6)
     return info, ref, tr_gpu, tr_ref, dX
 
 
@@ -131,3 +140,50 @@ def test_resolve_with_new_rhs_is_repeatable():
         s.solve()
         Z2, Y2, g2_ = s.factors()
     assert np.array_equal(Z1, Z2) and np.array_equal(Y1, Y2) and np.array_equal(g1, g2_)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("name,strategy,jacobi", [("small2d", "nobl_mid", False), ("tiny2d", "bl_mid", True)])
+def test_mixed_precision_parity(precision, name, strategy, jacobi):
+    """Krylov basis and sweeps in float32 (or a bfloat16 basis), restart
+    residuals, least squares and the outer iteration in float64: same outer
+    steps as the float64 oracle (+-1) and the same factored solution."""
+    compare(problem(name), strategy, jacobi, precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_mixed_precision_complex_pairs(precision):
+    p = W.make_problem("cplx", 14, 2, "rot2", 60.0, 12, 2, "rot2", 40.0, 2, 33, 8, real_shifts=False)
+    info, ref, tr_gpu, tr_ref, dX = compare(p, "bl_mid", True, precision=precision)
+    assert info["is_complex"] == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["tiny2d", "small2d"])
+def test_graph_and_host_driven_solves_agree_bitwise(precision, name):
+    """The device-driven CUDA graph (conditional nodes set by the kernels) and
+    the host-driven loop launch the same kernels in the same order; with the
+    fixed-order reductions the factors agree bit for bit."""
+    p = problem(name)
+    jac = int(p.opts.get("jacobi", False))
+    out = []
+    for driver in (0, 1):
+        st, info, hist, Z, Y, gam = run_gpu(p, strategy="nobl_mid", jacobi=jac, precision=precision,
+                                            driver=driver)
+        assert st == 0
+        out.append((info["steps"], Z, Y, gam, info["launches"]))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[0][3], out[1][3])
+    # the graph skips the restart kernels in iterations that do not need them
+    assert 0 < out[0][4] <= out[1][4]
+
+
+def test_graph_solve_respects_kmax_and_zero_rhs():
+    p = problem("small2d")
+    with P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, kmax=2, jacobi=0, driver=0) as s:
+        assert s.solve() == -4
+        assert s.info()["steps"] == 2
+    with P.SylvesterADI(p.A, p.B, np.zeros_like(p.f), p.g, p.alpha, p.beta, p.tau, driver=0) as s:
+        assert s.solve() == 0
+        assert s.info()["steps"] == 0

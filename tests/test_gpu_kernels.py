@@ -221,3 +221,37 @@ def test_controller_matches_oracle(lib, strategy, clamp):
         assert out[i, 1] == pytest.approx(dB, rel=1e-13, abs=0)
         if strategy != "fixed":
             assert out[i, 2] == pytest.approx(eh, rel=1e-13, abs=0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind", ["tiny2d_A", "tiny2d_Bt", "small3d"])
+def test_gmres_mixed_precision_meets_tolerance(torch_cuda, precision, kind):
+    """float32/bfloat16 basis: the float64 restart residual still reaches tol
+    (iterative refinement across restarts) and the solution matches the
+    oracle's float64 solve to the accuracy both reached."""
+    torch = torch_cuda
+    M, sigma, tr = _gmres_case(kind)
+    S = M.to_scipy()
+    St = S.T.tocsr() if tr else S
+    n = S.shape[0]
+    cplx = isinstance(sigma, complex)
+    rng = np.random.default_rng(8)
+    Bm = rng.standard_normal((n, 2))
+    if cplx:
+        Bm = Bm + 1j * rng.standard_normal((n, 2))
+    tol = 1e-10 * np.linalg.norm(Bm[:, 0])
+    op = P.sylv_op_create(M, transpose=tr)
+    try:
+        dB = _colmajor(torch, Bm)
+        dX = torch.zeros_like(dB)
+        rc, iters, res, _ = P.sylv_gmres(op, sigma, 1, cplx, dB, dX, 2, tol, 30, 6000,
+                                         precision=precision)
+        X = _host(dX).T
+    finally:
+        P.sylv_op_destroy(op)
+    assert rc == 0
+    for c in range(2):
+        rr = np.linalg.norm(Bm[:, c] - shifted_apply(St, sigma, X[:, c]))
+        assert rr <= tol * (1 + 1e-6)
+        ref = ogmres(St, sigma, Bm[:, c], tol, 30, 6000, True, "cgs2")
+        assert np.linalg.norm(X[:, c] - ref.x) <= 1e3 * tol / abs(sigma) * 10 + 1e-12
