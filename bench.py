@@ -294,12 +294,15 @@ def run_ours(a):
     # ---- comparison runs: mixed precision, fixed 1e-12 float64 ----
     variants = {}
     if not a.no_variants:
-        for name, kw, w_, k_ in (("fp32_basis", dict(strategy=a.strategy, precision="fp32"), 1, 2),
-                                 ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2),
-                                 ("fp64_fixed_1e-12", dict(strategy="fixed", fixed_tol=1e-12,
-                                                           precision="fp64"), 0, 1)):
+        for name, kw, w_, k_, prof in (
+                ("fp32_basis", dict(strategy=a.strategy, precision="fp32"), 1, 2, True),
+                ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2, True),
+                ("fp64_fixed_1e-12", dict(strategy="fixed", fixed_tol=1e-12, precision="fp64"), 0, 1, True),
+                # one CUDA graph per solve, device-set conditional nodes (no kernel events)
+                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False),
+                ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 2, False)):
             sv = make(**kw)
-            tv, stv = timed(sv, w_, k_, profile=True)
+            tv, stv = timed(sv, w_, k_, profile=prof)
             variants[name], _, _ = summary(sv, tv, stv)
             variants[name]["strategy"] = kw["strategy"]
             sv.close()

@@ -138,6 +138,10 @@ __device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_
 __device__ __forceinline__ cplx shfl_xor(cplx v, int m) {
     return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
 }
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ cflt shfl_xor(cflt v, int m) {
+    return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
 __device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ cplx shfl_idx(cplx v, int src) {
     return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};

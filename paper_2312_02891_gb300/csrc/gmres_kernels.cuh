@@ -119,15 +119,17 @@ __device__ void mark_done(SysState<T>* st, BatchCtl* ctl) {
 typedef double RedBufD[SYLV_NWARP][PSTRIDE];
 
 // Per-thread accumulators (type A, NV slots) -> block sums in type T written to
-// out[0..cnt); red is a shared buffer of SYLV_NWARP x PSTRIDE T.
+// out[0..cnt); red is a shared buffer of SYLV_NWARP x PSTRIDE T.  The warp
+// stage adds in A (float32 for the mixed path: float64 adds run at 1/58 of
+// the float32 rate on this GPU); warps and chunks are combined in T.
 template <typename T, typename A, int NV>
 __device__ __forceinline__ void block_reduce_to(A (&acc)[NV], int cnt, T* out, T (*red)[PSTRIDE]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < NV; ++l) {
         if (l < cnt) {
-            T v = warp_sum(cvt<T>(acc[l]));
-            if (lane == 0) red[warp][l] = v;
+            const A v = warp_sum(acc[l]);
+            if (lane == 0) red[warp][l] = cvt<T>(v);
         }
     }
     __syncthreads();
@@ -144,11 +146,17 @@ template <int NV, typename T, typename S, typename C>
 __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDesc& op, const SysState<T>* st,
                                           int j, typename RealOf<C>::type sj, int r0, int r1, int mode,
                                           T* out, T (*red)[PSTRIDE]) {
-    const S* __restrict__ vj = sd.V + (size_t)j * sd.ldv;
+    // the basis, the work vector and the operator never overlap: tell the
+    // compiler, so the loads of the next row can overlap this row's store
+    const S* __restrict__ V = sd.V;
+    C* __restrict__ w = sd.w;
+    const size_t ldv = sd.ldv;
+    const S* __restrict__ vj = V + (size_t)j * ldv;
     const C* __restrict__ av = sd.aval;
     C acc[NV];
 #pragma unroll
     for (int l = 0; l < NV; ++l) acc[l] = zero<C>();
+#pragma unroll 2
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C wi;
         if (mode == 0) {
@@ -171,13 +179,13 @@ __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDe
                 });
                 wi = cvt<C>(acc64);
             }
-            sd.w[i] = wi;
+            w[i] = wi;
         } else {
-            wi = sd.w[i];
+            wi = w[i];
         }
 #pragma unroll
         for (int l = 0; l < NV; ++l)
-            if (l <= j) acc[l] += cmul(cvt<C>(sd.V[(size_t)l * sd.ldv + i]), wi);
+            if (l <= j) acc[l] += cmul(cvt<C>(V[(size_t)l * ldv + i]), wi);
     }
     block_reduce_to<T, C, NV>(acc, j + 1, out, red);
 }
@@ -226,17 +234,20 @@ k_arnoldi_spmv(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restric
 template <int NV, typename T, typename S, typename C>
 __device__ __forceinline__ void pass2_rows(const SysDesc<T, S, C>& sd, const C* cc, int j, int r0, int r1,
                                            T* out, T (*red)[PSTRIDE]) {
+    const S* __restrict__ V = sd.V;
+    const C* __restrict__ w = sd.w;
+    const size_t ldv = sd.ldv;
     C acc[NV];
 #pragma unroll
     for (int l = 0; l < NV; ++l) acc[l] = zero<C>();
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        C w1 = sd.w[i];
+        C w1 = w[i];
 #pragma unroll
         for (int l = 0; l < NV; ++l)
-            if (l <= j) w1 -= cc[l] * cvt<C>(sd.V[(size_t)l * sd.ldv + i]);
+            if (l <= j) w1 -= cc[l] * cvt<C>(V[(size_t)l * ldv + i]);
 #pragma unroll
         for (int l = 0; l < NV; ++l)
-            if (l <= j) acc[l] += cmul(cvt<C>(sd.V[(size_t)l * sd.ldv + i]), w1);
+            if (l <= j) acc[l] += cmul(cvt<C>(V[(size_t)l * ldv + i]), w1);
     }
     block_reduce_to<T, C, NV>(acc, j + 1, out, red);
 }
@@ -426,13 +437,17 @@ __device__ __forceinline__ void cgs_pass3_body(const SysDesc<T, S, C>* __restric
     __syncthreads();
     const int r0 = it.chunk * sd.rows_per_chunk;
     const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
-    S* __restrict__ vn = sd.V + (size_t)(j + 1) * sd.ldv;
+    // vectors 0..j are read, vector j+1 is written: disjoint ranges
+    const S* __restrict__ V = sd.V;
+    const C* __restrict__ w = sd.w;
+    const size_t ldv = sd.ldv;
+    S* __restrict__ vn = sd.V + (size_t)(j + 1) * ldv;
     CR acc[1] = {(CR)0};
 #define SYLV_PASS3_CALL(NV)                                                   \
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {                 \
-        C x = sd.w[i];                                                        \
+    _Pragma("unroll 2") for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) { \
+        C x = w[i];                                                           \
         _Pragma("unroll") for (int l = 0; l < NV; ++l)                        \
-            if (l <= j) x -= cc[l] * cvt<C>(sd.V[(size_t)l * sd.ldv + i]);    \
+            if (l <= j) x -= cc[l] * cvt<C>(V[(size_t)l * ldv + i]);          \
         const S xs = cvt<S>(x);                                               \
         vn[i] = xs;                                                           \
         acc[0] += abs2(cvt<C>(xs));                                           \

@@ -68,7 +68,7 @@ def compare(p, strategy, jacobi, xtol=1e-6, **extra):
         # (back-looking tolerances follow the achieved inner residuals, which
         # float32 inner solves change within their tolerances)
         assert h[12] == pytest.approx(o["res_comp"], rel=0.05 if mixed else 1e-3, abs=1e-3 * p.tau)
-        assert h[13] == pytest.approx(o["N_w"], rel=1e-3 if mixed else 1e-6)
+        assert h[13] == pytest.approx(o["N_w"], rel=1e-2 if mixed else 1e-6)
     return info, ref, tr_gpu, tr_ref, dX
 
 
