@@ -48,6 +48,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """The job's time: the largest per-rank value over the default process
+    group (replicas; no data-path collective exists in the solver)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,11 +252,7 @@ def run_ours(a):
         barrier()
         solver.timed_solves = steps
         t = sum(s.elapsed_time(e) for s, e in ev) / 1e3 / steps
-        if ws > 1:
-            tt = torch.tensor([t], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t = float(tt.item())
-        return t, st
+        return max_over_ranks(t, "cuda"), st
 
     def summary(solver, t, st):
         info = solver.info()

@@ -45,6 +45,25 @@ def true_residual_norm2(A, B, f, g, Z, gamma, Y) -> float:
     return lowrank_norm2(U, W)
 
 
+def sampled_residual(A, B, f, g, Z, gamma, Y, rows, cols) -> np.ndarray:
+    """Entries R[rows][:, cols] of R = A X + X B + f g^* for X = Z diag(gamma) Y^*,
+    evaluated exactly from the sparsity of A and B (for factors too large to
+    form R): (A X)_ij uses X at the nonzero columns of row i of A, (X B)_ij
+    uses X at the nonzero rows of column j of B."""
+    A = A.tocsr()
+    Bc = B.tocsc()
+    rows = np.asarray(rows)
+    cols = np.asarray(cols)
+    nr = np.unique(np.concatenate([A.indices[A.indptr[i]:A.indptr[i + 1]] for i in rows] + [rows]))
+    nc = np.unique(np.concatenate([Bc.indices[Bc.indptr[j]:Bc.indptr[j + 1]] for j in cols] + [cols]))
+    G = gamma[:, None] * Y[cols].conj().T            # kr x |cols|
+    XA = Z[nr] @ G                                    # X[nr, cols]
+    XB = Z[rows] @ (gamma[:, None] * Y[nc].conj().T)  # X[rows, nc]
+    Ar = A[rows][:, nr]
+    Bs = Bc[nc][:, cols]
+    return Ar @ XA + XB @ Bs + f[rows] @ g[cols].conj().T
+
+
 def factored_diff_fro(Z1, g1, Y1, Z2, g2, Y2) -> float:
     """||Z1 diag(g1) Y1^* - Z2 diag(g2) Y2^*||_F."""
     U = np.hstack([Z1 * g1[None, :], -Z2 * g2[None, :]])

@@ -296,13 +296,29 @@ class Problem:
         return self.f.shape[1]
 
 
+INVERSE_RITZ_MAX_N = 600_000     # above this the LU of the operator is too costly
+
+
+def _inverse_ritz(op: CSR, N: int, dim: int, kind: str, mag: float, steps: int) -> np.ndarray:
+    """Inverse Ritz values of the operator, or - when it is too large for a
+    sparse LU - of the same convection-diffusion family discretised on a
+    coarser grid (the small eigenvalues of the differential operator, which
+    these approximate, change little with the grid)."""
+    if op.n <= INVERSE_RITZ_MAX_N:
+        return inverse_ritz_values(op, steps)
+    Nc = int(round(INVERSE_RITZ_MAX_N ** (1.0 / dim) / 2))
+    return inverse_ritz_values(convdiff(Nc, dim, kind, mag), steps)
+
+
 def make_problem(name, NA, dimA, kindA, magA, NB, dimB, kindB, magB, r, seed,
                  n_shifts, real_shifts=True, tau=1e-8, ritz_steps=20, **opts) -> Problem:
     A = convdiff(NA, dimA, kindA, magA)
     B = convdiff(NB, dimB, kindB, magB)
     f, g = rhs_factors(A.n, B.n, r, seed)
-    cand_a = np.concatenate([ritz_values(A, ritz_steps), inverse_ritz_values(A, ritz_steps)])
-    cand_b = np.concatenate([ritz_values(B, ritz_steps), inverse_ritz_values(B, ritz_steps)])
+    cand_a = np.concatenate([ritz_values(A, ritz_steps),
+                             _inverse_ritz(A, NA, dimA, kindA, magA, ritz_steps)])
+    cand_b = np.concatenate([ritz_values(B, ritz_steps),
+                             _inverse_ritz(B, NB, dimB, kindB, magB, ritz_steps)])
     alpha, beta = select_shift_pairs(cand_a, cand_b, n_shifts, real=real_shifts)
     return Problem(name, A, B, f, g, alpha, beta, tau, dict(opts))
 
@@ -316,7 +332,24 @@ def problem_config(which: str) -> Problem:
       seed 1, 12 real shift pairs, right-Jacobi GMRES(30).
     * "tiny2d": A 2D N=12, omega=10(x,y); B 2D N=10, omega=5(y,-x); r=2,
       seed 7 (unit-test size).
+    * "mid3d": A 3D N=128 (n = 2097152), omega=100(1,1,1); B 3D N=100
+      (m = 1000000), omega=50(z,x,y); r=4, seed 2, 16 shift pairs kept complex
+      (conjugate pairs adjacent), right-Jacobi GMRES(30).
+    * "large3d": A 3D N=256 (n = 16777216), omega=200(x,y,z); B 3D N=192
+      (m = 7077888), omega=100(y,-x,0); r=1, seed 3, 20 complex shift pairs,
+      right-Jacobi GMRES(20).
+    * "small3d": A 3D N=24, omega=100(1,1,1); B 3D N=20, omega=50(z,x,y);
+      r=4, seed 4, 8 complex shift pairs (test size of the 3D family).
     """
+    if which == "mid3d":
+        return make_problem("mid3d", 128, 3, "const3", 100.0, 100, 3, "zxy", 50.0, 4, 2, 16,
+                            real_shifts=False, restart=30, jacobi=True)
+    if which == "large3d":
+        return make_problem("large3d", 256, 3, "xyz", 200.0, 192, 3, "rot3", 100.0, 1, 3, 20,
+                            real_shifts=False, restart=20, jacobi=True)
+    if which == "small3d":
+        return make_problem("small3d", 24, 3, "const3", 100.0, 20, 3, "zxy", 50.0, 4, 4, 8,
+                            real_shifts=False, restart=30, jacobi=True)
     if which == "small2d":
         return make_problem("small2d", 32, 2, "xy", 10.0, 30, 2, "rot2", 5.0, 1, 0, 12,
                             restart=30, jacobi=False)

@@ -108,6 +108,14 @@ def test_complex_shift_pairs_parity():
     assert info["is_complex"] == 1
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small3d_complex_parity(precision):
+    """3D operators with rotational convection, r = 4, complex conjugate shift
+    pairs (the family of the large 3D workloads, at a size the oracle runs)."""
+    info, ref, tr_gpu, tr_ref, dX = compare(problem("small3d"), "nobl_mid", True, precision=precision)
+    assert info["is_complex"] == 1 and tr_gpu <= 1e-8
+
+
 def test_zero_rhs_is_solved_by_zero():
     p = problem("tiny2d")
     z = np.zeros_like(p.f)

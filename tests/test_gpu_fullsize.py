@@ -89,6 +89,28 @@ def test_mid2d_matches_stored_oracle(mid, sketcher, gname, opts, xtol):
         assert tot == pytest.approx(g["inner_its_A"] + g["inner_its_B"], rel=0.02)
 
 
+def test_mid3d_complex_mixed_precision_sampled_residual():
+    """3D workload with complex conjugate shift pairs (A: n = 2097152, B: m =
+    1000000, r = 4), complex64 Krylov basis and sweeps, float64 outer
+    iteration.  Too large for the oracle's full run: the oracle evaluates
+    sampled entries of the true residual exactly from the GPU factors, and
+    the sampled solution entries must be real (conjugate pairs)."""
+    from oracle.residual import sampled_residual
+    p = W.problem_config("mid3d")
+    st, info, hist, (Z, Y, gam) = solve(p, strategy="nobl_mid", precision="fp32", driver=0)
+    assert st == 0, P.sylv_last_error()
+    assert info["is_complex"] == 1 and info["rel_res_comp"] < p.tau
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(p.A.n, 64, replace=False))
+    cols = np.sort(rng.choice(p.B.n, 64, replace=False))
+    nfg = lowrank_norm2(p.f, p.g)
+    R = sampled_residual(p.A.to_scipy(), p.B.to_scipy(), p.f, p.g, Z, gam, Y, rows, cols)
+    assert np.abs(R).max() <= p.tau * nfg
+    X = Z[rows] @ (gam[:, None] * Y[cols].conj().T)
+    # inexact solves break the conjugate symmetry only at the level of their tolerances
+    assert np.abs(X.imag).max() <= 1e-5 * np.abs(X.real).max()
+
+
 def test_mid2d_literal_back_looking_stagnates_like_the_oracle(mid):
     """With eq. (ADI_relax2_prak) taken literally the tolerances outgrow ||w||
     on this workload and the iteration stalls near 3e-7 at kmax = 50; the GPU

@@ -190,6 +190,16 @@ def test_theorem1_and_2_inexact(tiny):
     assert gap <= res.history[-1]["u"] + res.history[-1]["v"] + 1e-20
 
 
+def test_sampled_residual_matches_dense(tiny):
+    from oracle.residual import sampled_residual
+    res = lradi(tiny.A, tiny.B, tiny.f, tiny.g, tiny.alpha, tiny.beta, tiny.tau, strategy="bl_mid", kmax=4)
+    A, B = tiny.A.to_scipy(), tiny.B.to_scipy()
+    R = dense_residual(A, B, tiny.f, tiny.g, X_of(res))
+    rows, cols = np.array([0, 5, 17, 143]), np.array([0, 3, 50, 99])
+    S = sampled_residual(A, B, tiny.f, tiny.g, res.Z, res.gamma, res.Y, rows, cols)
+    assert np.allclose(S, R[np.ix_(rows, cols)], rtol=1e-12, atol=1e-14 * np.abs(R).max())
+
+
 def test_lowrank_norms_match_dense(tiny):
     rng = np.random.default_rng(4)
     U, V = rng.standard_normal((50, 3)), rng.standard_normal((40, 3))
