@@ -163,6 +163,27 @@ int sylv_op_destroy(sylv_op* op);
 int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out,
               int32_t is_complex, void* stream);
 
+/* The same CGS2 step for callers that cannot let a library allocate GPU
+ * memory (a pool or arena that owns the device budget, loops that must not
+ * allocate after start-up, custom memory managers).  The paper has no
+ * counterpart; this is a library service.  Real data only.
+ * V: device, n x (k + 1), column-major (ld = n); columns 0..k-1 hold the
+ * orthonormal basis, column k receives the orthogonalised w divided by its
+ * norm.  w: device, n entries, read only.  h_out: host, k + 1 entries, as for
+ * sylv_cgs2.  1 <= k <= 30 and n <= sylv_cgs2_noalloc_max_rows().
+ * Scratch lives in one static device array of SYLV_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits; no
+ * cudaMalloc/cudaFree or other allocating call is made.  The first call on
+ * a device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and each call re-initialises what it reads, so calls
+ * that overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  Sizes beyond the limit return SYLV_ERR_INVALID with a message. */
+#define SYLV_NOALLOC_SCRATCH_BYTES (1 << 20)
+int sylv_cgs2_noalloc(double* V, int32_t n, int32_t k, const double* w, double* h_out, void* stream);
+/* Largest n sylv_cgs2_noalloc accepts. */
+int sylv_cgs2_noalloc_max_rows(void);
+
 /* ------------------------------------------------------------------------ */
 /* Batched shifted GMRES (steps a2-a7)                                       */
 /* ------------------------------------------------------------------------ */

@@ -37,7 +37,7 @@ EXPORTED = (
     "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval", "sylv_adi_create",
     "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
     "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "sylv_adi_profile",
-    "sylv_adi_kernel_stats",
+    "sylv_adi_kernel_stats", "sylv_cgs2_noalloc", "sylv_cgs2_noalloc_max_rows",
 )
 KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3", "restart_update", "restart_residual",
            "adi_controller", "adi_step_init", "adi_gram")
@@ -119,6 +119,8 @@ def load():
         "sylv_adi_destroy": ([vp], C.c_int),
         "sylv_adi_profile": ([vp, i32], C.c_int),
         "sylv_adi_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
+        "sylv_cgs2_noalloc": ([vp, i32, i32, vp, pd, vp], C.c_int),
+        "sylv_cgs2_noalloc_max_rows": ([], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -223,6 +225,21 @@ def sylv_cgs2(V, n, k, w, is_complex=False, stream=None) -> np.ndarray:
     _check(load().sylv_cgs2(_ptr(V), int(n), int(k), _ptr(w), h.ctypes.data, int(is_complex),
                             _stream(stream)))
     return h.view(np.complex128) if is_complex else h
+
+
+def sylv_cgs2_noalloc(V, n, k, w, stream=None) -> np.ndarray:
+    """CGS2 step that allocates no GPU memory (static scratch in the library).
+
+    V: device n x (k+1) float64, column-major; column k receives the
+    normalised result.  w: device n float64 (read only).  Returns h (k+1)."""
+    h = np.zeros(k + 1)
+    _check(load().sylv_cgs2_noalloc(_ptr(V), int(n), int(k), _ptr(w),
+                                    h.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+    return h
+
+
+def sylv_cgs2_noalloc_max_rows() -> int:
+    return int(load().sylv_cgs2_noalloc_max_rows())
 
 
 def sylv_gmres(op, sigma, jacobi, is_complex, B, X, ncols, tol, restart, max_iters,

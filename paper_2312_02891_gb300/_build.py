@@ -17,7 +17,8 @@ CSRC = PKG / "csrc"
 OUT = PKG / "_lib"
 OBJ = PKG / "_lib" / "obj"
 LIB = OUT / "libsylv_adi.so"
-SOURCES = ["api.cu", "ops.cu", "inst_r64.cu", "inst_r32.cu", "inst_rbf.cu", "inst_c128.cu", "inst_c64.cu", "inst_cbf.cu"]
+SOURCES = ["api.cu", "ops.cu", "inst_r64.cu", "inst_r32.cu", "inst_rbf.cu", "inst_c128.cu", "inst_c64.cu",
+           "inst_cbf.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
