@@ -269,6 +269,50 @@ int sylv_adi_profile(sylv_handle* h, int32_t enable);
 int sylv_adi_kernel_stats(const sylv_handle* h, double* ms, double* bytes, double* flops,
                           int64_t* launches);
 
+/* ------------------------------------------------------------------------ */
+/* Batched solves: many independent equations in one device loop            */
+/* ------------------------------------------------------------------------ */
+/* One equation A X + X B = -f g^* of a batch, with its own sizes, rank,
+ * shift pairs and tolerance (the arguments of sylv_adi_create). */
+typedef struct sylv_problem {
+    const sylv_csr* A;
+    const sylv_csr* B;
+    const double* f;            /* n x r, host */
+    const double* g;            /* m x r, host */
+    int32_t r;
+    const sylv_shift* alpha;    /* n_shifts pairs, host */
+    const sylv_shift* beta;
+    int32_t n_shifts;
+    double tol;
+} sylv_problem;
+
+typedef struct sylv_batch sylv_batch;
+
+/* Every instance runs Algorithm 1 with the same options (opts may be NULL;
+ * dmin and fixed_tol defaults follow each instance's tol).  The 2 r_i column
+ * systems of all instances share each GMRES sweep launch and instances move
+ * between outer steps independently, so a solve is one CUDA graph launch with
+ * no host round trip (opts->driver is ignored).  If any instance has complex
+ * shifts the whole batch runs in complex arithmetic.  Pointers are borrowed
+ * for the call.  Errors as sylv_adi_create, the message naming the instance. */
+int sylv_adi_batch_create(int32_t count, const sylv_problem* probs, const sylv_opts* opts, void* stream,
+                          sylv_batch** out);
+/* Solve all instances (blocks until done).  SYLV_OK when every instance
+ * reached its tolerance, else the status of the first instance that did not
+ * (sylv_adi_batch_info gives each instance's status). */
+int sylv_adi_batch_solve(sylv_batch* b);
+/* Per instance i (0 <= i < count): as sylv_adi_info / _history / _factors.
+ * ticks and launches in the info are those of the whole batch solve. */
+int sylv_adi_batch_info(const sylv_batch* b, int32_t i, sylv_info* info);
+int sylv_adi_batch_history(const sylv_batch* b, int32_t i, double* buf, int32_t cap, int32_t* rows);
+int sylv_adi_batch_factors(const sylv_batch* b, int32_t i, void* Z, void* Y, void* gamma, int32_t on_device,
+                           int32_t* kr_out, int32_t* is_complex);
+/* Whole-batch counters since create: kernel launches and device iterations
+ * of the last solve; algorithmic bytes and flops of all kernels. */
+int sylv_adi_batch_stats(const sylv_batch* b, int64_t* launches, double* bytes, double* flops,
+                         int64_t* ticks);
+int sylv_adi_batch_destroy(sylv_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,9 @@ __all__ = [
     "sylv_adi_create", "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve",
     "sylv_adi_info", "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "SylvesterADI",
     "sylv_adi_profile", "sylv_adi_kernel_stats", "HIST_COLUMNS", "EXPORTED", "KERNELS",
+    "SylvProblem", "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info",
+    "sylv_adi_batch_history", "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy",
+    "SylvesterADIBatch",
 ]
 
 SYLV_OK = 0
@@ -38,6 +41,8 @@ EXPORTED = (
     "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
     "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "sylv_adi_profile",
     "sylv_adi_kernel_stats", "sylv_cgs2_noalloc", "sylv_cgs2_noalloc_max_rows",
+    "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info", "sylv_adi_batch_history",
+    "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy",
 )
 KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3", "restart_update", "restart_residual",
            "adi_controller", "adi_step_init", "adi_gram")
@@ -65,6 +70,12 @@ class SylvOpts(C.Structure):
                 ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
                 ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32)]
+
+
+class SylvProblem(C.Structure):
+    _fields_ = [("A", C.POINTER(SylvCsr)), ("B", C.POINTER(SylvCsr)), ("f", C.c_void_p),
+                ("g", C.c_void_p), ("r", C.c_int32), ("alpha", C.c_void_p), ("beta", C.c_void_p),
+                ("n_shifts", C.c_int32), ("tol", C.c_double)]
 
 
 class SylvInfo(C.Structure):
@@ -121,6 +132,13 @@ def load():
         "sylv_adi_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "sylv_cgs2_noalloc": ([vp, i32, i32, vp, pd, vp], C.c_int),
         "sylv_cgs2_noalloc_max_rows": ([], C.c_int),
+        "sylv_adi_batch_create": ([i32, C.POINTER(SylvProblem), C.POINTER(SylvOpts), vp, C.POINTER(vp)], C.c_int),
+        "sylv_adi_batch_solve": ([vp], C.c_int),
+        "sylv_adi_batch_info": ([vp, i32, C.POINTER(SylvInfo)], C.c_int),
+        "sylv_adi_batch_history": ([vp, i32, pd, i32, pi32], C.c_int),
+        "sylv_adi_batch_factors": ([vp, i32, vp, vp, vp, i32, pi32, pi32], C.c_int),
+        "sylv_adi_batch_stats": ([vp, C.POINTER(C.c_int64), pd, pd, C.POINTER(C.c_int64)], C.c_int),
+        "sylv_adi_batch_destroy": ([vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -386,6 +404,123 @@ class SylvesterADI:
     def close(self) -> None:
         if self.h:
             sylv_adi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---- batched solves ----
+
+def sylv_adi_batch_create(problems, opts: SylvOpts | None = None, stream=None):
+    """problems: sequence of (A, B, f, g, alpha, beta, tau).  Returns (handle,
+    keep) where keep holds the host arrays alive for the call."""
+    keep = []
+    arr = (SylvProblem * len(problems))()
+    for i, (A, B, f, g, alpha, beta, tau) in enumerate(problems):
+        ha, hb = _csr(A), _csr(B)
+        f = np.asfortranarray(f, dtype=np.float64)
+        g = np.asfortranarray(g, dtype=np.float64)
+        if f.shape[1] != g.shape[1] or len(alpha) != len(beta):
+            raise ValueError(f"instance {i}: f/g columns or shift counts differ")
+        al = (SylvShift * len(alpha))(*[_shift(a) for a in alpha])
+        be = (SylvShift * len(beta))(*[_shift(b) for b in beta])
+        keep += [ha, hb, f, g, al, be]
+        arr[i] = SylvProblem(C.pointer(ha.s), C.pointer(hb.s), f.ctypes.data, g.ctypes.data, f.shape[1],
+                             C.addressof(al), C.addressof(be), len(alpha), float(tau))
+    out = C.c_void_p()
+    _check(load().sylv_adi_batch_create(len(problems), arr, C.byref(opts) if opts is not None else None,
+                                        _stream(stream), C.byref(out)))
+    return out.value
+
+
+def sylv_adi_batch_solve(b) -> int:
+    """Solves every instance; returns the batch status (0, or MAXIT/INNER_STALL warnings)."""
+    return _check(load().sylv_adi_batch_solve(b), allow_warn=True)
+
+
+def sylv_adi_batch_info(b, i: int) -> dict:
+    info = SylvInfo()
+    _check(load().sylv_adi_batch_info(b, int(i), C.byref(info)))
+    return info.as_dict()
+
+
+def sylv_adi_batch_history(b, i: int, cap: int = 1000) -> np.ndarray:
+    buf = np.zeros((cap, len(HIST_COLUMNS)))
+    rows = C.c_int32()
+    _check(load().sylv_adi_batch_history(b, int(i), buf.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                         C.byref(rows)))
+    return buf[: rows.value]
+
+
+def sylv_adi_batch_factors(b, i: int, n: int, m: int):
+    info = sylv_adi_batch_info(b, i)
+    kr, cplx = info["kr"], info["is_complex"]
+    dt = np.complex128 if cplx else np.float64
+    Z = np.zeros((kr, n), dtype=dt)
+    Y = np.zeros((kr, m), dtype=dt)
+    gam = np.zeros(kr, dtype=dt)
+    kro, isc = C.c_int32(), C.c_int32()
+    _check(load().sylv_adi_batch_factors(b, int(i), Z.ctypes.data, Y.ctypes.data, gam.ctypes.data, 0,
+                                         C.byref(kro), C.byref(isc)))
+    return Z.T, Y.T, gam
+
+
+def sylv_adi_batch_stats(b) -> dict:
+    la, ti = C.c_int64(), C.c_int64()
+    by, fl = C.c_double(), C.c_double()
+    _check(load().sylv_adi_batch_stats(b, C.byref(la), C.byref(by), C.byref(fl), C.byref(ti)))
+    return {"launches": la.value, "bytes": by.value, "flops": fl.value, "ticks": ti.value}
+
+
+def sylv_adi_batch_destroy(b) -> None:
+    _check(load().sylv_adi_batch_destroy(b))
+
+
+class SylvesterADIBatch:
+    """Many independent A_i X + X B_i = -f_i g_i^* solved in one device loop.
+
+    problems: objects with fields A, B, f, g, alpha, beta, tau (for example
+    workloads.Problem) or tuples in that order."""
+
+    def __init__(self, problems, stream=None, **opts):
+        tup = [p if isinstance(p, tuple) else (p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau) for p in problems]
+        self.sizes = [(t[0].n if hasattr(t[0], "n") else t[0].shape[0],
+                       t[1].n if hasattr(t[1], "n") else t[1].shape[0]) for t in tup]
+        self.opts = sylv_opts_default(**opts)
+        self.h = sylv_adi_batch_create(tup, self.opts, stream)
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def solve(self) -> int:
+        return sylv_adi_batch_solve(self.h)
+
+    def info(self, i: int) -> dict:
+        return sylv_adi_batch_info(self.h, i)
+
+    def history(self, i: int) -> np.ndarray:
+        return sylv_adi_batch_history(self.h, i)
+
+    def factors(self, i: int):
+        n, m = self.sizes[i]
+        return sylv_adi_batch_factors(self.h, i, n, m)
+
+    def stats(self) -> dict:
+        return sylv_adi_batch_stats(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            sylv_adi_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -57,6 +57,7 @@ template <typename T>
 struct AdiState {
     int k;                  // current outer step (1-based)
     int done;
+    int stage;              // batched solves: where this instance stands (BatchStage)
     int status;             // 0 ok, 1 maxit, 2 nonfinite
     int pair_open;          // inside a conjugate shift pair
     unsigned counter;
@@ -184,25 +185,13 @@ __device__ __forceinline__ bool is_pair_start(const T* alpha, const T* beta, int
     return re(a1) == re(a) && im(a1) == -im(a) && re(b1) == re(b) && im(b1) == -im(b);
 }
 
-// Start of outer step k: tolerances, shifts and the 2r column solves.
+// Start of outer step k of one instance: tolerances (Sec. 3.3), the shift
+// pair and the 2r column systems, left in the restart phase so that their
+// first device iteration forms r = b - (Op + sigma I) x with x = 0.
 template <typename T, typename S, typename C>
-__global__ void k_adi_controller(AdiDev<T, S, C> d) {
-    count_launch(d.ctl, K_CTRL);
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void adi_begin_step(const AdiDev<T, S, C>& d) {
     AdiState<T>* s = d.s;
     const int r = d.r;
-    // graph-driven solve: no further outer step unless the factor update asks
-    if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_outer, 0u);
-    if (s->done) {
-        for (int q = 0; q < 2 * r; ++q) d.st[q].phase = PH_DONE;
-        d.ctl->n_active = 0;
-        if (d.ctl->h_flag) { *(volatile int*)d.ctl->h_flag = 0; __threadfence_system(); }
-        if (d.ctl->graph) {
-            cudaGraphSetConditional(d.ctl->h_loop, 0u);
-            cudaGraphSetConditional(d.ctl->h_outer, 0u);
-        }
-        return;
-    }
     const int k = s->k;
     const int idx = (k - 1) % d.nshift;
     const T a = d.alpha[idx], b = d.beta[idx];
@@ -233,6 +222,27 @@ __global__ void k_adi_controller(AdiDev<T, S, C> d) {
             st.b = d.t + (size_t)l * d.m;
         }
     }
+}
+
+template <typename T, typename S, typename C>
+__global__ void k_adi_controller(AdiDev<T, S, C> d) {
+    count_launch(d.ctl, K_CTRL);
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    AdiState<T>* s = d.s;
+    const int r = d.r;
+    // graph-driven solve: no further outer step unless the factor update asks
+    if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_outer, 0u);
+    if (s->done) {
+        for (int q = 0; q < 2 * r; ++q) d.st[q].phase = PH_DONE;
+        d.ctl->n_active = 0;
+        if (d.ctl->h_flag) { *(volatile int*)d.ctl->h_flag = 0; __threadfence_system(); }
+        if (d.ctl->graph) {
+            cudaGraphSetConditional(d.ctl->h_loop, 0u);
+            cudaGraphSetConditional(d.ctl->h_outer, 0u);
+        }
+        return;
+    }
+    adi_begin_step(d);
     d.ctl->n_active = 2 * r;
     d.ctl->ticks = 0;
     if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_loop, 1u);
@@ -242,12 +252,10 @@ __global__ void k_adi_controller(AdiDev<T, S, C> d) {
 // Z and Y, form the Jacobi inverse 1 / (diag + sigma) for the new shift and
 // the pre-scaled stencil diagonals of (Op + sigma I) P^{-1}.
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T, S, C> d) {
-    count_launch(d.ctl, K_STEP);
+__device__ __forceinline__ void adi_step_rows(const AdiDev<T, S, C>& d, int bi) {
     const AdiState<T>* s = d.s;
-    if (s->done) return;
-    const bool sideA = (int)blockIdx.x < d.nchA;
-    const int chunk = sideA ? blockIdx.x : blockIdx.x - d.nchA;
+    const bool sideA = bi < d.nchA;
+    const int chunk = sideA ? bi : bi - d.nchA;
     const int nn = sideA ? d.n : d.m;
     const int r0 = chunk * d.rpc, r1 = min(nn, r0 + d.rpc);
     const T sigma = sideA ? s->beta_k : conjg(s->alpha_k);
@@ -264,6 +272,13 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T, S, C> d)
         for (int l = 0; l < d.r; ++l) X[(size_t)l * nn + i] = zero<T>();
 }
 
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_step_init(AdiDev<T, S, C> d) {
+    count_launch(d.ctl, K_STEP);
+    if (d.s->done) return;
+    adi_step_rows(d, blockIdx.x);
+}
+
 // Gram partials of three n x r blocks (P, Q, R): G[a][b] = sum_i conj(P_a) P_b.
 template <typename T>
 __device__ __forceinline__ void gram_acc(T* G, const T* v, int r) {
@@ -278,13 +293,13 @@ __device__ __forceinline__ void gram_acc(T* G, const T* v, int r) {
 // Gamma), then the residual norm ||w_k t_k^*|| = sqrt(lambda_max(G_w G_t)),
 // eq. (upd_resgap) and the outer stop test ||w_k t_k^*|| < tau ||f g^*||.
 // init = 1: w_0 = f, t_0 = g and the norms of the right-hand side.
+// Block bi (of nchA + nchB) of one instance; true in the one thread that
+// finished the step (thread 0 of the instance's last block).
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int init) {
-    count_launch(d.ctl, K_GRAM);
+__device__ bool adi_gram_body(const AdiDev<T, S, C>& d, int init, int bi) {
     AdiState<T>* s = d.s;
-    if (!init && s->done) return;
-    const bool sideA = (int)blockIdx.x < d.nchA;
-    const int chunk = sideA ? blockIdx.x : blockIdx.x - d.nchA;
+    const bool sideA = bi < d.nchA;
+    const int chunk = sideA ? bi : bi - d.nchA;
     const int nn = sideA ? d.n : d.m;
     const int r = d.r;
     const int r0 = chunk * d.rpc, r1 = min(nn, r0 + d.rpc);
@@ -319,7 +334,7 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int 
             for (int l = 0; l < SYLV_MAXR; ++l) {
                 if (l < r) {
                     zv[l] = X[(size_t)l * nn + i];
-                    rv[l] = cvt<T>(sd[l].V[i]);
+                    rv[l] = cvt<T>(sd[l].V[BasisIx<1>::row(sd[l], i)]);
                     wv[l] = W[(size_t)l * nn + i] + gm * zv[l];
                     W[(size_t)l * nn + i] = wv[l];
                 }
@@ -330,12 +345,12 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int 
         }
     }
     block_reduce_store<T, T, 3 * SYLV_MAXR * SYLV_MAXR>(G, 3 * SYLV_MAXR * SYLV_MAXR,
-                                                      d.gpart + (size_t)blockIdx.x * SYLV_GSTRIDE);
-    if (!last_block(&s->counter, d.nchA + d.nchB)) return;
+                                                      d.gpart + (size_t)bi * SYLV_GSTRIDE);
+    if (!last_block(&s->counter, d.nchA + d.nchB)) return false;
     __shared__ T GA[SYLV_GSTRIDE], GB[SYLV_GSTRIDE];
     reduce_chunks(d.gpart, d.nchA, SYLV_GSTRIDE, SYLV_GSTRIDE, GA);
     reduce_chunks(d.gpart + (size_t)d.nchA * SYLV_GSTRIDE, d.nchB, SYLV_GSTRIDE, SYLV_GSTRIDE, GB);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0) return false;
     s->counter = 0;
     const int RR = SYLV_MAXR * SYLV_MAXR;
     if (init) {
@@ -387,6 +402,15 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int 
         else if (!s->pair_open && res < d.tau * s->nfg) { s->done = 1; s->status = 0; }
         else if (s->k > d.kmax) { s->done = 1; s->status = 1; }
     }
+    return true;
+}
+
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK) k_adi_gram(AdiDev<T, S, C> d, int init) {
+    count_launch(d.ctl, K_GRAM);
+    AdiState<T>* s = d.s;
+    if (!init && s->done) return;
+    if (!adi_gram_body(d, init, blockIdx.x)) return;
     if (d.h_done) { *(volatile int*)d.h_done = s->done; __threadfence_system(); }
     if (d.ctl->graph) cudaGraphSetConditional(d.ctl->h_outer, s->done ? 0u : 1u);
 }

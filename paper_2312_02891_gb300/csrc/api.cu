@@ -13,6 +13,66 @@ using namespace sylv;
 
 static bool shift_is_complex(sylv_shift s) { return s.im != 0.0; }
 
+// Arguments of one problem (shared by the single and the batched create):
+// sizes, tolerance, finite shifts, conjugate pairs adjacent.
+static int check_problem(const double* f, const double* g, int32_t r, const sylv_shift* alpha,
+                         const sylv_shift* beta, int32_t n_shifts, double tol, bool* cplx_out) {
+    if (!f || !g || !alpha || !beta || n_shifts <= 0) {
+        set_error("null f/g/shifts or n_shifts <= 0");
+        return SYLV_ERR_INVALID;
+    }
+    if (r < 1 || r > SYLV_MAX_RANK) {
+        set_error("rank r=%d outside 1..%d", r, SYLV_MAX_RANK);
+        return r < 1 ? SYLV_ERR_INVALID : SYLV_ERR_UNSUPPORTED;
+    }
+    if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must lie in (0, 1)"); return SYLV_ERR_INVALID; }
+    bool cplx = false;
+    for (int i = 0; i < n_shifts; ++i) {
+        if (!std::isfinite(alpha[i].re) || !std::isfinite(alpha[i].im) || !std::isfinite(beta[i].re) ||
+            !std::isfinite(beta[i].im)) {
+            set_error("non-finite shift %d", i);
+            return SYLV_ERR_INVALID;
+        }
+        cplx |= shift_is_complex(alpha[i]) || shift_is_complex(beta[i]);
+    }
+    if (cplx) {
+        // conjugate pairs must be adjacent: a complex pair at i is followed by its conjugate
+        for (int i = 0; i < n_shifts; ++i) {
+            if (!(shift_is_complex(alpha[i]) || shift_is_complex(beta[i]))) continue;
+            if (i + 1 >= n_shifts || alpha[i + 1].re != alpha[i].re || alpha[i + 1].im != -alpha[i].im ||
+                beta[i + 1].re != beta[i].re || beta[i + 1].im != -beta[i].im) {
+                set_error("complex shift pair %d is not followed by its conjugate pair", i);
+                return SYLV_ERR_INVALID;
+            }
+            ++i;
+        }
+    }
+    *cplx_out = cplx;
+    return SYLV_OK;
+}
+
+// Options with the tolerance-dependent defaults filled in, validated.
+static int resolve_opts(const sylv_opts* opts, double tol, sylv_opts* o) {
+    if (opts) *o = *opts; else sylv_opts_default(o);
+    if (o->dmin_A <= 0) o->dmin_A = tol / 20;
+    if (o->dmin_B <= 0) o->dmin_B = tol / 20;
+    if (o->fixed_tol <= 0) o->fixed_tol = tol / 20;
+    if (o->restart < 1 || o->restart > SYLV_MAX_RESTART) {
+        set_error("restart %d outside 1..%d", o->restart, SYLV_MAX_RESTART);
+        return SYLV_ERR_UNSUPPORTED;
+    }
+    if (o->kmax < 1 || o->max_inner < 1 || o->strategy < 0 || o->strategy > SYLV_STRAT_BL_B ||
+        !(o->xi > 0.0 && o->xi <= 1.0) || !(o->dmax_A > 0) || !(o->dmax_B > 0)) {
+        set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
+        return SYLV_ERR_INVALID;
+    }
+    if (o->precision < SYLV_PREC_FP64 || o->precision > SYLV_PREC_BF16) {
+        set_error("precision %d not built", o->precision);
+        return SYLV_ERR_UNSUPPORTED;
+    }
+    return SYLV_OK;
+}
+
 extern "C" {
 
 const char* sylv_last_error(void) { return last_error_cstr(); }
@@ -103,51 +163,11 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
                     double tol, const sylv_opts* opts, void* stream, sylv_handle** out) {
     if (!out) { set_error("sylv_adi_create: null out"); return SYLV_ERR_INVALID; }
     *out = nullptr;
-    if (!f || !g || !alpha || !beta || n_shifts <= 0) {
-        set_error("sylv_adi_create: null f/g/shifts or n_shifts <= 0");
-        return SYLV_ERR_INVALID;
-    }
-    if (r < 1 || r > SYLV_MAX_RANK) {
-        set_error("rank r=%d outside 1..%d", r, SYLV_MAX_RANK);
-        return r < 1 ? SYLV_ERR_INVALID : SYLV_ERR_UNSUPPORTED;
-    }
-    if (!(tol > 0.0 && tol < 1.0)) { set_error("tol must lie in (0, 1)"); return SYLV_ERR_INVALID; }
     sylv_opts o;
-    if (opts) o = *opts; else sylv_opts_default(&o);
-    if (o.dmin_A <= 0) o.dmin_A = tol / 20;
-    if (o.dmin_B <= 0) o.dmin_B = tol / 20;
-    if (o.fixed_tol <= 0) o.fixed_tol = tol / 20;
-    if (o.restart < 1 || o.restart > SYLV_MAX_RESTART) {
-        set_error("restart %d outside 1..%d", o.restart, SYLV_MAX_RESTART);
-        return SYLV_ERR_UNSUPPORTED;
-    }
-    if (o.kmax < 1 || o.max_inner < 1 || o.strategy < 0 || o.strategy > SYLV_STRAT_BL_B ||
-        !(o.xi > 0.0 && o.xi <= 1.0) || !(o.dmax_A > 0) || !(o.dmax_B > 0)) {
-        set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
-        return SYLV_ERR_INVALID;
-    }
-    if (o.precision < SYLV_PREC_FP64 || o.precision > SYLV_PREC_BF16) { set_error("precision %d not built", o.precision); return SYLV_ERR_UNSUPPORTED; }
     bool cplx = false;
-    for (int i = 0; i < n_shifts; ++i) {
-        if (!std::isfinite(alpha[i].re) || !std::isfinite(alpha[i].im) || !std::isfinite(beta[i].re) ||
-            !std::isfinite(beta[i].im)) {
-            set_error("non-finite shift %d", i);
-            return SYLV_ERR_INVALID;
-        }
-        cplx |= shift_is_complex(alpha[i]) || shift_is_complex(beta[i]);
-    }
-    if (cplx) {
-        // conjugate pairs must be adjacent: a complex pair at i is followed by its conjugate
-        for (int i = 0; i < n_shifts; ++i) {
-            if (!(shift_is_complex(alpha[i]) || shift_is_complex(beta[i]))) continue;
-            if (i + 1 >= n_shifts || alpha[i + 1].re != alpha[i].re || alpha[i + 1].im != -alpha[i].im ||
-                beta[i + 1].re != beta[i].re || beta[i + 1].im != -beta[i].im) {
-                set_error("complex shift pair %d is not followed by its conjugate pair", i);
-                return SYLV_ERR_INVALID;
-            }
-            ++i;
-        }
-    }
+    int vrc = check_problem(f, g, r, alpha, beta, n_shifts, tol, &cplx);
+    if (vrc == SYLV_OK) vrc = resolve_opts(opts, tol, &o);
+    if (vrc != SYLV_OK) return vrc;
     sylv_handle* h = new (std::nothrow) sylv_handle();
     if (!h) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
     h->stream = (cudaStream_t)stream;
@@ -225,6 +245,112 @@ int sylv_adi_destroy(sylv_handle* h) {
     h->A.release();
     h->Bt.release();
     delete h;
+    return SYLV_OK;
+}
+
+// ---- batched solves ----
+
+static void release_batch(sylv_batch* b) {
+    if (!b) return;
+    delete b->impl;
+    for (auto& op : b->ops) op.release();
+    delete b;
+}
+
+int sylv_adi_batch_create(int32_t count, const sylv_problem* probs, const sylv_opts* opts, void* stream,
+                          sylv_batch** out) {
+    if (!out) { set_error("sylv_adi_batch_create: null out"); return SYLV_ERR_INVALID; }
+    *out = nullptr;
+    if (count < 1 || !probs) { set_error("batch: count %d < 1 or null problems", count); return SYLV_ERR_INVALID; }
+    sylv_opts o;
+    bool cplx = false;
+    std::vector<sylv_opts> per(count);
+    for (int i = 0; i < count; ++i) {
+        const sylv_problem& p = probs[i];
+        bool ci = false;
+        int rc = check_problem(p.f, p.g, p.r, p.alpha, p.beta, p.n_shifts, p.tol, &ci);
+        if (rc == SYLV_OK) rc = resolve_opts(opts, p.tol, &per[i]);
+        if (rc != SYLV_OK) {
+            const std::string msg = last_error_cstr();
+            set_error("batch instance %d: %s", i, msg.c_str());
+            return rc;
+        }
+        cplx |= ci;
+    }
+    o = per[0];
+    sylv_batch* b = new (std::nothrow) sylv_batch();
+    if (!b) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
+    b->count = count;
+    b->is_complex = cplx ? 1 : 0;
+    b->stream = (cudaStream_t)stream;
+    b->ops.resize(2 * (size_t)count);
+    std::vector<BatchProb> ps(count);
+    int rc = SYLV_OK;
+    for (int i = 0; i < count && rc == SYLV_OK; ++i) {
+        HostCsr ha, hb, hbt;
+        rc = load_csr(probs[i].A, ha);
+        if (rc == SYLV_OK) rc = load_csr(probs[i].B, hb);
+        if (rc == SYLV_OK) { transpose_csr(hb, hbt); rc = b->ops[2 * i].upload(ha); }
+        if (rc == SYLV_OK) rc = b->ops[2 * i + 1].upload(hbt);
+        if (rc != SYLV_OK) {
+            const std::string msg = last_error_cstr();
+            set_error("batch instance %d: %s", i, msg.c_str());
+            break;
+        }
+        const sylv_problem& p = probs[i];
+        ps[i] = BatchProb{&b->ops[2 * i], &b->ops[2 * i + 1], ha.n, hb.n, p.r, p.f, p.g, p.alpha, p.beta,
+                          p.n_shifts, p.tol, per[i].dmin_A, per[i].dmin_B, per[i].fixed_tol};
+    }
+    if (rc == SYLV_OK) {
+        auto mk = cplx ? (o.precision == SYLV_PREC_FP32 ? make_batch_c64 : o.precision == SYLV_PREC_BF16 ? make_batch_cbf : make_batch_c128)
+                       : (o.precision == SYLV_PREC_FP32 ? make_batch_r32 : o.precision == SYLV_PREC_BF16 ? make_batch_rbf : make_batch_r64);
+        rc = mk(ps, o, b->stream, &b->impl);
+    }
+    if (rc != SYLV_OK) {
+        release_batch(b);
+        return rc;
+    }
+    *out = b;
+    return SYLV_OK;
+}
+
+int sylv_adi_batch_solve(sylv_batch* b) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    return b->impl->solve();
+}
+
+static int batch_index(const sylv_batch* b, int32_t i) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    if (i < 0 || i >= b->count) { set_error("instance %d outside 0..%d", i, b->count - 1); return SYLV_ERR_INVALID; }
+    return SYLV_OK;
+}
+
+int sylv_adi_batch_info(const sylv_batch* b, int32_t i, sylv_info* info) {
+    SYLV_TRY(batch_index(b, i));
+    if (!info) { set_error("null info"); return SYLV_ERR_INVALID; }
+    return b->impl->info(i, info);
+}
+
+int sylv_adi_batch_history(const sylv_batch* b, int32_t i, double* buf, int32_t cap, int32_t* rows) {
+    SYLV_TRY(batch_index(b, i));
+    if (!buf && cap > 0) { set_error("null buffer"); return SYLV_ERR_INVALID; }
+    return b->impl->history(i, buf, cap, rows);
+}
+
+int sylv_adi_batch_factors(const sylv_batch* b, int32_t i, void* Z, void* Y, void* gamma, int32_t on_device,
+                           int32_t* kr_out, int32_t* is_complex) {
+    SYLV_TRY(batch_index(b, i));
+    if (is_complex) *is_complex = b->is_complex;
+    return b->impl->factors(i, Z, Y, gamma, on_device, kr_out);
+}
+
+int sylv_adi_batch_stats(const sylv_batch* b, int64_t* launches, double* bytes, double* flops, int64_t* ticks) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    return b->impl->stats((long long*)launches, bytes, flops, (long long*)ticks);
+}
+
+int sylv_adi_batch_destroy(sylv_batch* b) {
+    release_batch(b);
     return SYLV_OK;
 }
 

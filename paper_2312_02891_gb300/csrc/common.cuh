@@ -102,6 +102,14 @@ template <typename X> struct RealOf { typedef X type; };
 template <> struct RealOf<cplx> { typedef double type; };
 template <> struct RealOf<cflt> { typedef float type; };
 
+// Resident blocks per SM the basis sweeps are compiled for.  The 32-bit
+// sweeps are latency-bound (they need many loads in flight per SM, so more
+// resident warps); the float64 sweeps are bound by the float64 pipe and keep
+// their registers.
+template <typename C> struct SweepOcc { static constexpr int value = 1; };
+template <> struct SweepOcc<float> { static constexpr int value = 3; };
+template <> struct SweepOcc<cflt> { static constexpr int value = 2; };
+
 // ---------------------------------------------------------------------------
 // Conversions between the roles (storage <-> arithmetic <-> float64).
 // ---------------------------------------------------------------------------
@@ -205,7 +213,8 @@ struct SysDesc {
     int op;                 // index into the batch's operator table
     int nchunks;            // work units of this system
     int rows_per_chunk;
-    size_t ldv;             // stride between basis vectors
+    size_t ldv;             // column-major basis: stride between basis vectors
+    size_t tstride;         // tile-major basis: elements per 32-row tile (32 x vectors)
     S* V;                   // (restart + 1) basis vectors, stored unnormalised
     C* w;                   // Arnoldi work vector (operator output)
     T* part;                // nchunks x PSTRIDE partial sums
@@ -214,6 +223,24 @@ struct SysDesc {
     double* hist;           // optional: Givens estimate per Arnoldi step
     int hist_cap;
     int restart;
+};
+
+// Basis addressing.  Tile-major (LAY 1, the solver's own basis): rows are
+// grouped in tiles of 32, and a tile stores its 32 rows of every basis vector
+// contiguously, so the loads of one warp for all vectors of a row tile fall
+// in one small contiguous range (one page, not one page per vector) and the
+// per-vector offsets are compile-time constants off a single base pointer.
+// Column-major (LAY 0): vectors ldv apart, for callers' own buffers.
+template <int LAY> struct BasisIx;
+template <> struct BasisIx<0> {
+    template <class D> __device__ __forceinline__ static size_t row(const D& sd, int i) { return (size_t)i; }
+    template <class D> __device__ __forceinline__ static size_t vec(const D& sd, int l) { return (size_t)l * sd.ldv; }
+};
+template <> struct BasisIx<1> {
+    template <class D> __device__ __forceinline__ static size_t row(const D& sd, int i) {
+        return (size_t)(i >> 5) * sd.tstride + (size_t)(i & 31);
+    }
+    template <class D> __device__ __forceinline__ static size_t vec(const D&, int l) { return (size_t)l * 32; }
 };
 
 template <typename T>
@@ -266,6 +293,7 @@ struct BatchCtl {
     cudaGraphConditionalHandle h_restart;  // IF: restart kernels in this iteration
     cudaGraphConditionalHandle h_outer;    // WHILE: outer steps of Algorithm 1
     unsigned long long launch_count[K_COUNT];  // launches, counted by block 0 of each kernel
+    int n_inst_open;        // batched solves: instances not finished (0 for a single solve)
 };
 
 __device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {

@@ -36,6 +36,28 @@ template <typename T> struct Dev {
 
 inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
 
+// Rows per work item of the basis sweeps, in whole 32-row tiles, at least
+// 256 rows: one wave of resident blocks over all rows of the batch for the
+// 32-bit sweeps (several resident blocks per SM hide each other's fixed
+// costs; measured best on the 2D benchmark workload), two waves for the
+// float64 sweeps (one resident block per SM).
+template <typename T, typename S, typename C>
+int sweep_rows_per_chunk(long long total_rows) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_pass2<T, S, C>, SYLV_BLOCK, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long waves = SweepOcc<C>::value > 1 ? 1 : 2;
+    const long long items = waves * num_sms() * per_sm;
+    long long rpc = (total_rows + items - 1) / items;
+    rpc = (rpc + 31) / 32 * 32;
+    return (int)std::max<long long>(256, std::min<long long>(rpc, 1 << 16));
+}
+
+// Elements of one system's tile-major basis: whole 32-row tiles.
+template <class D>
+inline size_t basis_elems(const D& d) { return (size_t)((d.n + 31) / 32) * d.tstride; }
+
 // A batch of shifted systems solved together by restarted GMRES.
 template <typename T, typename S, typename C>
 struct Engine {
@@ -85,7 +107,8 @@ struct Engine {
         nsys = (int)sys_n.size();
         long long total_rows = 0;
         for (int q = 0; q < nsys; ++q) total_rows += sys_n[q];
-        if (rpc <= 0) rpc = auto_rows_per_chunk(total_rows);
+        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(total_rows);
+        rpc = (rpc + 31) / 32 * 32;       // chunks hold whole 32-row basis tiles
         size_t vtot = 0, wtot = 0, ptot = 0;
         std::vector<Item> items;
         h_sd.resize(nsys);
@@ -98,11 +121,12 @@ struct Engine {
             d.rows_per_chunk = rpc;
             d.nchunks = (sys_n[q] + rpc - 1) / rpc;
             d.ldv = round_ld(sys_n[q]);
+            d.tstride = (size_t)(restart + 1) * 32;
             d.restart = restart;
             d.hist = hist.empty() ? nullptr : hist[q];
             d.hist_cap = hist_cap;
             d.pinv = pinv[q];
-            vtot += (size_t)(restart + 1) * d.ldv;
+            vtot += basis_elems(d);
             wtot += d.ldv;
             ptot += (size_t)d.nchunks * PSTRIDE;
             for (int c = 0; c < d.nchunks; ++c) items.push_back({q, c});
@@ -117,7 +141,7 @@ struct Engine {
             d.V = d_V.p + vo;
             d.w = d_w.p + wo;
             d.part = d_part.p + po;
-            vo += (size_t)(restart + 1) * d.ldv;
+            vo += basis_elems(d);
             wo += d.ldv;
             po += (size_t)d.nchunks * PSTRIDE;
         }
@@ -262,10 +286,23 @@ int op_apply_t(const DevOp& op, T sigma, int jacobi, const void* X, void* Y, int
     return SYLV_OK;
 }
 
+// dst = scale * (column col of a tile-major basis with tile stride tstride).
 template <typename T>
-__global__ void k_copy_scaled(const T* __restrict__ src, double scale, T* __restrict__ dst, int n) {
+__global__ void k_copy_scaled(const T* __restrict__ V, size_t tstride, int col, double scale, T* __restrict__ dst,
+                              int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        dst[i] = scale * src[i];
+        dst[i] = scale * V[(size_t)(i >> 5) * tstride + (size_t)col * 32 + (i & 31)];
+}
+
+// Columns 0..k-1 of a column-major n x k block (leading dimension n) into a
+// tile-major basis.
+template <typename T>
+__global__ void k_to_tiles(const T* __restrict__ src, int n, int k, T* __restrict__ V, size_t tstride) {
+    const long long tot = (long long)n * k;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(q / n), i = (int)(q - (long long)l * n);
+        V[(size_t)(i >> 5) * tstride + (size_t)l * 32 + (i & 31)] = src[q];
+    }
 }
 
 // Stencil operators whose main diagonal is stored get the pre-scaled diagonals.
@@ -365,9 +402,8 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
     const std::vector<T*> pv{nullptr};
     SYLV_TRY(eng.setup(sn, so, ops, pv, std::vector<T*>(), std::vector<double*>(), 0, k, 0, s));
     const SysDesc<T, T, T>& d = eng.h_sd[0];
-    for (int l = 0; l < k; ++l)
-        SYLV_CK(cudaMemcpyAsync(d.V + (size_t)l * d.ldv, (const T*)V + (size_t)l * n, n * sizeof(T),
-                                cudaMemcpyDeviceToDevice, s));
+    k_to_tiles<T><<<num_sms() * 4, 256, 0, s>>>((const T*)V, n, k, d.V, d.tstride);
+    SYLV_CK(cudaGetLastError());
     SYLV_CK(cudaMemcpyAsync(d.w, w, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     SysState<T> st;
     std::memset(&st, 0, sizeof(st));
@@ -382,7 +418,7 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
     SYLV_TRY(eng.launch_tick(1));
     SYLV_CK(cudaStreamSynchronize(s));
     SYLV_CK(cudaMemcpy(&st, eng.d_st.p, sizeof(st), cudaMemcpyDeviceToHost));
-    k_copy_scaled<T><<<num_sms() * 4, 256, 0, s>>>(d.V + (size_t)k * d.ldv, st.scale[k], (T*)w, n);
+    k_copy_scaled<T><<<num_sms() * 4, 256, 0, s>>>(d.V, d.tstride, k, st.scale[k], (T*)w, n);
     SYLV_CK(cudaGetLastError());
     SYLV_CK(cudaStreamSynchronize(s));
     T* ho = (T*)h;
@@ -437,7 +473,7 @@ struct Adi : AdiBase {
         stream = a.stream;
         n = a.n; m = a.m; r = a.r; kmax = a.o.kmax; max_inner = a.o.max_inner;
         const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
-                                               : auto_rows_per_chunk((long long)(n + m) * r);
+                                               : sweep_rows_per_chunk<T, S, C>((long long)(n + m) * r);
         SYLV_TRY(f.alloc((size_t)n * r));
         SYLV_TRY(g.alloc((size_t)m * r));
         SYLV_TRY(w.alloc((size_t)n * r));

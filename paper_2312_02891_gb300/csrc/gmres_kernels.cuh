@@ -141,51 +141,78 @@ __device__ __forceinline__ void block_reduce_to(A (&acc)[NV], int cnt, T* out, T
     }
 }
 
+// Row i of w = (Op + sigma I) P^{-1} (sj * V_j): the pre-scaled stencil
+// diagonals in C precision, or the generic operator row in float64.
+template <int LAY, typename T, typename S, typename C>
+__device__ __forceinline__ C spmv_row(const SysDesc<T, S, C>& sd, const OpDesc& op, const SysState<T>* st,
+                                      const S* __restrict__ vj, typename RealOf<C>::type sj, int i) {
+    typedef BasisIx<LAY> BI;
+    const C* __restrict__ av = sd.aval;
+    if (av) {
+        C a = zero<C>();
+#pragma unroll
+        for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+            if (d < op.ndiag) {
+                const int k = i + op.offs[d];
+                if (k >= 0 && k < op.n) a += av[(size_t)d * op.n + i] * cvt<C>(vj[BI::row(sd, k)]);
+            }
+        }
+        return sj * a;
+    }
+    const T sigma = st->sigma;
+    const T* __restrict__ pinv = sd.pinv;
+    const T acc64 = op_row<T>(op, i, sigma, [&](int k) {
+        const T x = (double)sj * cvt<T>(vj[BI::row(sd, k)]);
+        return pinv ? pinv[k] * x : x;
+    });
+    return cvt<C>(acc64);
+}
+
 // Rows [r0, r1) of sweep 1 with NV >= j + 1 accumulators.
-template <int NV, typename T, typename S, typename C>
+template <int NV, int LAY, typename T, typename S, typename C>
 __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDesc& op, const SysState<T>* st,
                                           int j, typename RealOf<C>::type sj, int r0, int r1, int mode,
                                           T* out, T (*red)[PSTRIDE]) {
+    typedef BasisIx<LAY> BI;
     // the basis, the work vector and the operator never overlap: tell the
     // compiler, so the loads of the next row can overlap this row's store
     const S* __restrict__ V = sd.V;
     C* __restrict__ w = sd.w;
-    const size_t ldv = sd.ldv;
-    const S* __restrict__ vj = V + (size_t)j * ldv;
-    const C* __restrict__ av = sd.aval;
+    const S* __restrict__ vj = V + BI::vec(sd, j);
     C acc[NV];
 #pragma unroll
     for (int l = 0; l < NV; ++l) acc[l] = zero<C>();
+    if constexpr (SweepOcc<C>::value == 1) {
+        // float64: one pass, two rows in flight per thread (bound by the
+        // float64 pipe, registers are not the limit)
 #pragma unroll 2
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        C wi;
-        if (mode == 0) {
-            if (av) {
-                C a = zero<C>();
-#pragma unroll
-                for (int d = 0; d < SYLV_MAXDIAG; ++d) {
-                    if (d < op.ndiag) {
-                        const int k = i + op.offs[d];
-                        if (k >= 0 && k < op.n) a += av[(size_t)d * op.n + i] * cvt<C>(vj[k]);
-                    }
-                }
-                wi = sj * a;
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            C wi;
+            if (mode == 0) {
+                wi = spmv_row<LAY>(sd, op, st, vj, sj, i);
+                w[i] = wi;
             } else {
-                const T sigma = st->sigma;
-                const T* __restrict__ pinv = sd.pinv;
-                const T acc64 = op_row<T>(op, i, sigma, [&](int k) {
-                    const T x = (double)sj * cvt<T>(vj[k]);
-                    return pinv ? pinv[k] * x : x;
-                });
-                wi = cvt<C>(acc64);
+                wi = w[i];
             }
-            w[i] = wi;
-        } else {
-            wi = w[i];
-        }
+            const S* __restrict__ vr = V + BI::row(sd, i);
 #pragma unroll
-        for (int l = 0; l < NV; ++l)
-            if (l <= j) acc[l] += cmul(cvt<C>(V[(size_t)l * ldv + i]), wi);
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), wi);
+        }
+    } else {
+        // 32-bit sweeps: the product rows first, then the dot products over
+        // the same rows (each thread re-reads only the w entries it wrote),
+        // so neither loop carries the other's registers and more warps stay
+        // resident
+        if (mode == 0)
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = spmv_row<LAY>(sd, op, st, vj, sj, i);
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const C wi = w[i];
+            const S* __restrict__ vr = V + BI::row(sd, i);
+#pragma unroll
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), wi);
+        }
     }
     block_reduce_to<T, C, NV>(acc, j + 1, out, red);
 }
@@ -196,8 +223,8 @@ __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDe
 // (formed once per shift), so the product is ndiag fused multiply-adds.
 // mode 1: w is given (a plain CGS2 of w against V), no operator product.
 // ---------------------------------------------------------------------------
-template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+template <typename T, typename S, typename C, int LAY = 1>
+__global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_arnoldi_spmv(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
                const OpDesc* __restrict__ ops, const Item* __restrict__ items, BatchCtl* ctl, int mode) {
     typedef typename RealOf<C>::type CR;
@@ -220,7 +247,7 @@ k_arnoldi_spmv(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restric
         : (double)(j + 1) * sd.n * sizeof(S) + (double)sd.n * sizeof(C),
         FmaFlops<C>::v * ((mode == 0 ? (double)op.nnz : 0.0) + (double)(j + 1) * sd.n));
     T* out = sd.part + (size_t)it.chunk * PSTRIDE;
-#define SYLV_SPMV_CALL(NV) spmv_rows<NV, T, S, C>(sd, op, st, j, sj, r0, r1, mode, out, red)
+#define SYLV_SPMV_CALL(NV) spmv_rows<NV, LAY, T, S, C>(sd, op, st, j, sj, r0, r1, mode, out, red)
     SYLV_BUCKET_SWITCH(j, SYLV_SPMV_CALL)
 #undef SYLV_SPMV_CALL
     if (!last_block(&st->counter, sd.nchunks)) return;
@@ -231,23 +258,24 @@ k_arnoldi_spmv(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restric
 }
 
 // Rows [r0, r1) of sweep 2 with NV >= j + 1 accumulators.
-template <int NV, typename T, typename S, typename C>
+template <int NV, int LAY, typename T, typename S, typename C>
 __device__ __forceinline__ void pass2_rows(const SysDesc<T, S, C>& sd, const C* cc, int j, int r0, int r1,
                                            T* out, T (*red)[PSTRIDE]) {
+    typedef BasisIx<LAY> BI;
     const S* __restrict__ V = sd.V;
     const C* __restrict__ w = sd.w;
-    const size_t ldv = sd.ldv;
     C acc[NV];
 #pragma unroll
     for (int l = 0; l < NV; ++l) acc[l] = zero<C>();
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C w1 = w[i];
+        const S* __restrict__ vr = V + BI::row(sd, i);
 #pragma unroll
         for (int l = 0; l < NV; ++l)
-            if (l <= j) w1 -= cc[l] * cvt<C>(V[(size_t)l * ldv + i]);
+            if (l <= j) w1 -= cc[l] * cvt<C>(vr[BI::vec(sd, l)]);
 #pragma unroll
         for (int l = 0; l < NV; ++l)
-            if (l <= j) acc[l] += cmul(cvt<C>(V[(size_t)l * ldv + i]), w1);
+            if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), w1);
     }
     block_reduce_to<T, C, NV>(acc, j + 1, out, red);
 }
@@ -256,8 +284,8 @@ __device__ __forceinline__ void pass2_rows(const SysDesc<T, S, C>& sd, const C* 
 // Sweep 2: h2 = V^* (w - V h1).  The row of V is read twice; the second read
 // hits L1 (or registers).
 // ---------------------------------------------------------------------------
-template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+template <typename T, typename S, typename C, int LAY = 1>
+__global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_cgs_pass2(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
             const Item* __restrict__ items, BatchCtl* ctl) {
     __shared__ T red[SYLV_NWARP][PSTRIDE];
@@ -275,7 +303,7 @@ k_cgs_pass2(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__
     const int r0 = it.chunk * sd.rows_per_chunk;
     const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
     T* out = sd.part + (size_t)it.chunk * PSTRIDE;
-#define SYLV_PASS2_CALL(NV) pass2_rows<NV, T, S, C>(sd, cc, j, r0, r1, out, red)
+#define SYLV_PASS2_CALL(NV) pass2_rows<NV, LAY, T, S, C>(sd, cc, j, r0, r1, out, red)
     SYLV_BUCKET_SWITCH(j, SYLV_PASS2_CALL)
 #undef SYLV_PASS2_CALL
     if (!last_block(&st->counter, sd.nchunks)) return;
@@ -401,6 +429,8 @@ __device__ void graph_tail(BatchCtl* ctl, SysState<T>* sts, int kid) {
     }
     pend = __syncthreads_or(pend);
     act = __syncthreads_or(act);
+    // a batch goes on while an instance still has an outer step to take
+    act |= (*(volatile int*)&ctl->n_inst_open > 0);
     if (threadIdx.x != 0) return;
     if (kid == K_CGS3) {
         const int t = ++ctl->ticks;
@@ -420,7 +450,7 @@ __device__ void graph_tail(BatchCtl* ctl, SysState<T>* sts, int kid) {
     }
 }
 
-template <typename T, typename S, typename C>
+template <typename T, typename S, typename C, int LAY>
 __device__ __forceinline__ void cgs_pass3_body(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
                                                const Item* __restrict__ items, BatchCtl* ctl, int mode) {
     typedef typename RealOf<C>::type CR;
@@ -438,18 +468,19 @@ __device__ __forceinline__ void cgs_pass3_body(const SysDesc<T, S, C>* __restric
     const int r0 = it.chunk * sd.rows_per_chunk;
     const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
     // vectors 0..j are read, vector j+1 is written: disjoint ranges
+    typedef BasisIx<LAY> BI;
     const S* __restrict__ V = sd.V;
     const C* __restrict__ w = sd.w;
-    const size_t ldv = sd.ldv;
-    S* __restrict__ vn = sd.V + (size_t)(j + 1) * ldv;
+    S* __restrict__ vn = sd.V + BI::vec(sd, j + 1);
     CR acc[1] = {(CR)0};
 #define SYLV_PASS3_CALL(NV)                                                   \
     _Pragma("unroll 2") for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) { \
         C x = w[i];                                                           \
+        const size_t ri = BI::row(sd, i);                                     \
         _Pragma("unroll") for (int l = 0; l < NV; ++l)                        \
-            if (l <= j) x -= cc[l] * cvt<C>(V[(size_t)l * ldv + i]);          \
+            if (l <= j) x -= cc[l] * cvt<C>(V[ri + BI::vec(sd, l)]);          \
         const S xs = cvt<S>(x);                                               \
-        vn[i] = xs;                                                           \
+        vn[ri] = xs;                                                          \
         acc[0] += abs2(cvt<C>(xs));                                           \
     }
     SYLV_BUCKET_SWITCH(j, SYLV_PASS3_CALL)
@@ -475,11 +506,11 @@ __device__ __forceinline__ void cgs_pass3_body(const SysDesc<T, S, C>* __restric
     }
 }
 
-template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+template <typename T, typename S, typename C, int LAY = 1>
+__global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_cgs_pass3(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
             const Item* __restrict__ items, BatchCtl* ctl, int mode) {
-    cgs_pass3_body<T, S, C>(sysd, sts, items, ctl, mode);
+    cgs_pass3_body<T, S, C, LAY>(sysd, sts, items, ctl, mode);
     if (ctl->graph) graph_tail<T>(ctl, sts, K_CGS3);
 }
 
@@ -510,7 +541,7 @@ k_restart_update(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restr
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {                 \
         C s = zero<C>();                                                      \
         _Pragma("unroll") for (int l = 0; l < NV; ++l)                        \
-            if (l < k) s += cc[l] * cvt<C>(sd.V[(size_t)l * sd.ldv + i]);     \
+            if (l < k) s += cc[l] * cvt<C>(sd.V[BasisIx<1>::row(sd, i) + 32 * l]); \
         const T s64 = cvt<T>(s);                                              \
         x[i] += sd.pinv ? sd.pinv[i] * s64 : s64;                             \
     }
@@ -547,7 +578,7 @@ __device__ __forceinline__ void restart_residual_body(const SysDesc<T, S, C>* __
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const T ax = op_row<T>(op, i, sigma, [&](int k) { return x[k]; });
         const T r = b[i] - ax;
-        sd.V[i] = cvt<S>(r);
+        sd.V[BasisIx<1>::row(sd, i)] = cvt<S>(r);
         acc[0] += abs2(r);
     }
     block_reduce_store<double, double, 1>(acc, 1, reinterpret_cast<double*>(sd.part + (size_t)it.chunk * PSTRIDE));

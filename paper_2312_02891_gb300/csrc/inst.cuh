@@ -3,7 +3,7 @@
 // Each inst_*.cu includes this header after defining SYLV_SUFFIX, SYLV_T,
 // SYLV_S and SYLV_C, so the combinations compile in parallel.
 #pragma once
-#include "engine.cuh"
+#include "batch.cuh"
 
 namespace sylv {
 
@@ -20,6 +20,11 @@ namespace sylv {
 
 int SYLV_CAT(make_adi_, SYLV_SUFFIX)(const AdiArgs& a, AdiBase** out) {
     return make_adi_t<SYLV_T, SYLV_S, SYLV_C>(a, out);
+}
+
+int SYLV_CAT(make_batch_, SYLV_SUFFIX)(const std::vector<BatchProb>& ps, const sylv_opts& o, cudaStream_t s,
+                                       BatchBase** out) {
+    return make_batch_t<SYLV_T, SYLV_S, SYLV_C>(ps, o, s, out);
 }
 
 int SYLV_CAT(gmres_, SYLV_SUFFIX)(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,

@@ -52,7 +52,6 @@ struct DevOp {
 };
 
 int num_sms();
-int auto_rows_per_chunk(long long total_rows);
 
 // Type-erased entry points implemented for double (real shifts) and cplx.
 struct AdiBase {
@@ -80,6 +79,31 @@ struct AdiArgs {
     cudaStream_t stream;
 };
 
+// One instance of a batched solve; the operators are owned by the batch
+// handle.  dminA/dminB/fixed_tol are the options resolved for this instance's
+// tolerance.
+struct BatchProb {
+    const DevOp* A;
+    const DevOp* Bt;
+    int n, m, r;
+    const double* f;
+    const double* g;
+    const sylv_shift* alpha;
+    const sylv_shift* beta;
+    int nshift;
+    double tau;
+    double dminA, dminB, fixed_tol;
+};
+
+struct BatchBase {
+    virtual ~BatchBase() {}
+    virtual int solve() = 0;
+    virtual int info(int i, sylv_info* out) const = 0;
+    virtual int history(int i, double* buf, int cap, int* rows) const = 0;
+    virtual int factors(int i, void* Z, void* Y, void* gamma, int on_device, int* kr) const = 0;
+    virtual int stats(long long* launches, double* bytes, double* flops, long long* ticks) const = 0;
+};
+
 // One instantiation per (shift type, precision): r = real shifts, c = complex
 // shifts; 64/128 = float64 throughout, 32/64 = float32 basis and sweeps,
 // bf = bfloat16 basis with float32 sweeps.
@@ -87,7 +111,9 @@ struct AdiArgs {
     int make_adi_##SUFFIX(const AdiArgs& a, AdiBase** out);                                         \
     int gmres_##SUFFIX(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,       \
                        int ncols, double tol, int restart, int max_iters, int* iters, double* res, \
-                       double* hist, cudaStream_t s);
+                       double* hist, cudaStream_t s);                                                \
+    int make_batch_##SUFFIX(const std::vector<BatchProb>& ps, const sylv_opts& o, cudaStream_t s,      \
+                            BatchBase** out);
 SYLV_DECL_INST(r64)
 SYLV_DECL_INST(r32)
 SYLV_DECL_INST(rbf)
@@ -105,6 +131,14 @@ int controller_eval_dev(const sylv_opts* o, int count, const double* in, double*
 
 struct sylv_op {
     sylv::DevOp op;
+};
+
+struct sylv_batch {
+    sylv::BatchBase* impl = nullptr;
+    std::vector<sylv::DevOp> ops;     // A_i, B_i^T for instance i at 2i, 2i + 1
+    int count = 0;
+    int is_complex = 0;
+    cudaStream_t stream = nullptr;
 };
 
 struct sylv_handle {

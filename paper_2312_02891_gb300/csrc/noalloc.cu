@@ -135,9 +135,9 @@ extern "C" int sylv_cgs2_noalloc(double* V, int32_t n, int32_t k, const double* 
     auto* dop = reinterpret_cast<const OpDesc*>(base + L.op);
     auto* di = reinterpret_cast<Item*>(base + L.items);
     k_noalloc_items<<<std::max(1, std::min(num_sms(), (nchunks + 255) / 256)), 256, 0, s>>>(di, nchunks);
-    k_arnoldi_spmv<double, double, double><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, dop, di, dc, 1);
-    k_cgs_pass2<double, double, double><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, di, dc);
-    k_cgs_pass3<double, double, double><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, di, dc, 1);
+    k_arnoldi_spmv<double, double, double, 0><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, dop, di, dc, 1);
+    k_cgs_pass2<double, double, double, 0><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, di, dc);
+    k_cgs_pass3<double, double, double, 0><<<nchunks, SYLV_BLOCK, 0, s>>>(dd, ds, di, dc, 1);
     const int grid = std::max(1, std::min(num_sms() * 4, (n + 255) / 256));
     k_noalloc_scale<<<grid, 256, 0, s>>>(V + (size_t)k * n, ds, k, n);
     SYLV_CK(cudaGetLastError());

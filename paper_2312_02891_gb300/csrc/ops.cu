@@ -38,14 +38,6 @@ int num_sms() {
     return cached;
 }
 
-int auto_rows_per_chunk(long long total_rows) {
-    // Aim at about four work units per SM across the whole batch, in whole
-    // multiples of the block size.
-    long long target = (total_rows + (long long)num_sms() * 4 - 1) / ((long long)num_sms() * 4);
-    target = (target + SYLV_BLOCK - 1) / SYLV_BLOCK * SYLV_BLOCK;
-    return (int)std::max<long long>(512, std::min<long long>(target, 1 << 16));
-}
-
 int load_csr(const sylv_csr* c, HostCsr& h) {
     if (!c) { set_error("null CSR descriptor"); return SYLV_ERR_INVALID; }
     if (c->n_rows <= 0 || c->n_rows != c->n_cols) {

@@ -362,15 +362,17 @@ def problem_config(which: str) -> Problem:
     raise ValueError(f"unknown workload {which!r}")
 
 
-def batch_problems(count: int, base_seed: int = 1000, n_shifts: int = 10):
-    """Independent 2D instances with N_A, N_B ~ U{64..256}, r in {1,2,4},
-    convection magnitudes ~ U[0,50] (directions (x,y) for A, (y,-x) for B)."""
+def batch_problems(count: int, base_seed: int = 1000, n_shifts: int = 10, nmin: int = 64, nmax: int = 256):
+    """Independent 2D instances with N_A, N_B ~ U{nmin..nmax} (64..256 for the
+    batched workload), r in {1,2,4}, convection magnitudes ~ U[0,50]
+    (directions (x,y) for A, (y,-x) for B); instance i uses seed base_seed + i."""
     out = []
+    span = nmax - nmin + 1
     for i in range(count):
         s = base_seed + i
         u = _uniform53(s, 9, 0, 0, 5)
-        NA = 64 + int(u[0] * 193)
-        NB = 64 + int(u[1] * 193)
+        NA = nmin + int(u[0] * span)
+        NB = nmin + int(u[1] * span)
         r = (1, 2, 4)[int(u[2] * 3)]
         magA, magB = 50.0 * u[3], 50.0 * u[4]
         out.append(make_problem(f"batch{i}", NA, 2, "xy", magA, NB, 2, "rot2", magB, r, s,

@@ -74,6 +74,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     # restart beyond the build limit
     o = P.sylv_opts_default(restart=31)
     assert lib.sylv_adi_create(C.byref(s), C.byref(s), pd, pd, 1, sh, sh, 1, 1e-8, C.byref(o), None, C.byref(out)) == -8
+    # batch: empty batch, and a bad instance named in the message
+    assert lib.sylv_adi_batch_create(0, None, None, None, C.byref(out)) == -1
+    probs = (P.SylvProblem * 2)(
+        P.SylvProblem(C.pointer(s), C.pointer(s), f.ctypes.data, f.ctypes.data, 1, C.addressof(sh), C.addressof(sh), 1, 1e-8),
+        P.SylvProblem(C.pointer(s), C.pointer(s), f.ctypes.data, f.ctypes.data, 1, C.addressof(shc), C.addressof(shc), 1, 1e-8))
+    assert lib.sylv_adi_batch_create(2, probs, None, None, C.byref(out)) == -1
+    assert "instance 1" in P.sylv_last_error() and "conjugate" in P.sylv_last_error()
+    # a null batch handle
+    assert lib.sylv_adi_batch_solve(None) == -1
+    assert lib.sylv_adi_batch_destroy(None) == 0
 
 
 def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
