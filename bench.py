@@ -6,8 +6,11 @@ factor updates, Gram residual norms, device controller) on the mid-size 2D
 convection-diffusion workload: A from N=512 (n = 262144, omega = 50 (x, y)),
 B from N=400 (m = 160000, omega = 20 (y, -x)), r = 2, 12 real shift pairs,
 right-Jacobi GMRES(30), "mid" tolerances without back-looking, tau = 1e-8,
-float64.  The line also carries the float32-basis and bfloat16-basis runs
-and the float64 run with a fixed inner tolerance of 1e-12.
+mixed precision (float32 Krylov basis and sweeps, float64 restart residuals,
+least squares, factors and outer iteration).  The line also carries the
+plain float64 run, the float64 run with a fixed inner tolerance of 1e-12,
+the bfloat16-basis run, the graph-driven runs and the batched workload (64
+independent instances in one device loop).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 bounded samples of the same workload instead.
@@ -40,8 +43,9 @@ def parse():
     ap.add_argument("--strategy", default="nobl_mid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
-                    help="precision of the headline solve (the benchmark line uses fp64)")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"],
+                    help="precision of the headline solve (the benchmark line uses fp32: float32 "
+                         "Krylov basis and sweeps, float64 outer iteration)")
     ap.add_argument("--kmax", type=int, default=50,
                     help="outer step cap (a small value gives a short case for profilers)")
     ap.add_argument("--cpu-sample-its", type=int, default=60)
@@ -198,6 +202,10 @@ def run_reference(a):
 
 
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 float64 rate (nominal, dense)
+SWEEPS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
+# DRAM traffic / algorithmic bytes of the sweep kernels from one ncu capture
+# of the current kernels (None once a kernel changes after its capture)
+NCU_TRAFFIC_RATIO = {}
 
 
 def run_ours(a):
@@ -215,6 +223,11 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     p = W.problem_config(a.workload)
+    # the 64 batched instances are generated on a host thread meanwhile
+    # (shift selection runs sparse LU solves; the solver calls release the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(max_workers=1)
+    batch_future = None if a.no_variants else pool.submit(W.batch_problems, 64)
     stream = torch.cuda.Stream()
     jac = int(p.opts.get("jacobi", False))
     rst = p.opts.get("restart", 30)
@@ -257,9 +270,8 @@ def run_ours(a):
     def summary(solver, t, st):
         info = solver.info()
         stats = solver.kernel_stats()
-        so = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
-        so_ms = sum(stats[k][0] for k in so)
-        so_by = sum(stats[k][1] for k in so)
+        so_ms = sum(stats[k][0] for k in SWEEPS)
+        so_by = sum(stats[k][1] for k in SWEEPS)
         return {"s": t, "status": st, "outer_steps": info["steps"], "inner_its_A": info["inner_its_A"],
                 "inner_its_B": info["inner_its_B"], "rel_res_comp": info["rel_res_comp"],
                 "launches_per_solve": info["launches"], "ticks_per_solve": info["ticks"],
@@ -267,8 +279,31 @@ def run_ours(a):
                 "kernel_ms_per_solve": {k: round(v[0] / max(1, solver.timed_solves), 2)
                                         for k, v in stats.items() if v[3] > 0}}, info, stats
 
-    # ---- headline: float64 inexact LR-ADI, adaptive tolerances ----
-    solver = make(strategy=a.strategy, precision=a.precision)
+    def kernel_table(stats):
+        total_ms = sum(v[0] for v in stats.values())
+        return {k: {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
+                    "launches": v[3],
+                    "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None,
+                    "TFLOPs": round(v[2] / (v[0] * 1e-3) / 1e12, 4) if v[0] > 0 else None}
+                for k, v in stats.items()}
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh_:
+            peaks = json.load(fh_)
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs, copy kernel)" if hbm else "fallback 6800 GB/s"
+    hbm = hbm or 6800.0
+
+    # ---- headline: mixed precision (float32 Krylov basis and sweeps, float64
+    # outer iteration), adaptive inner tolerances; host driver with CUDA
+    # events on every 4th device iteration for the per-kernel times ----
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    solver = make(strategy=a.strategy, precision=a.precision, driver=1)
+    torch.cuda.synchronize()
+    footprint = free0 - torch.cuda.mem_get_info()[0]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -296,63 +331,96 @@ def run_ours(a):
                                   C.byref(kro), C.byref(isc))
         e2e.append(time.perf_counter() - t0)
     barrier()
-    e2e_v = sum(e2e) / len(e2e)
+    e2e_v = max_over_ranks(sum(e2e) / len(e2e), "cuda")
     solver.close()
 
-    # ---- comparison runs: mixed precision, fixed 1e-12 float64 ----
+    # ---- comparison runs ----
     variants = {}
     if not a.no_variants:
         for name, kw, w_, k_, prof in (
-                ("fp32_basis", dict(strategy=a.strategy, precision="fp32"), 1, 2, True),
-                ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2, True),
+                ("fp64", dict(strategy=a.strategy, precision="fp64"), 1, 2, True),
                 ("fp64_fixed_1e-12", dict(strategy="fixed", fixed_tol=1e-12, precision="fp64"), 0, 1, True),
+                ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2, True),
                 # one CUDA graph per solve, device-set conditional nodes (no kernel events)
-                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False),
-                ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 2, False)):
+                ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 3, False),
+                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False)):
             sv = make(**kw)
             tv, stv = timed(sv, w_, k_, profile=prof)
-            variants[name], _, _ = summary(sv, tv, stv)
+            variants[name], _, vst = summary(sv, tv, stv)
             variants[name]["strategy"] = kw["strategy"]
+            if name == "fp64":
+                # the float64 sweeps are bound by the float64 pipe
+                dk = max(SWEEPS, key=lambda k_: vst[k_][0])
+                ms_, by_, fl_, la_ = vst[dk]
+                tf = (fl_ / la_) / ((ms_ / la_) * 1e-3) / 1e12
+                variants[name]["roofline"] = {"bound": "alu", "kernel": dk, "achieved": tf,
+                                              "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                              "frac": tf / FP64_NOMINAL_TFLOPS}
             sv.close()
-        variants["speedup_fp64_adaptive_vs_fp64_fixed_1e-12"] = variants["fp64_fixed_1e-12"]["s"] / t_solve
-        variants["speedup_fp32_adaptive_vs_fp64_fixed_1e-12"] = variants["fp64_fixed_1e-12"]["s"] / variants["fp32_basis"]["s"]
+        fixed = variants["fp64_fixed_1e-12"]["s"]
+        variants["speedup_mixed_adaptive_vs_fp64_fixed_1e-12"] = fixed / t_solve
+        variants["speedup_mixed_adaptive_graph_vs_fp64_fixed_1e-12"] = fixed / variants["fp32_graph"]["s"]
+        variants["speedup_fp64_adaptive_vs_fp64_fixed_1e-12"] = fixed / variants["fp64"]["s"]
 
-    # ---- roofline of the dominant kernel (float64: bound by the FP64 pipe) ----
-    dom = max((k for k in stats if stats[k][3] > 0), key=lambda k: stats[k][0])
+        # ---- batched workload: 64 independent 2D instances in one device loop ----
+        probs = batch_future.result()
+        for prec in ("fp32", "fp64"):
+            with P.SylvesterADIBatch(probs, stream=stream, strategy=a.strategy, precision=prec, jacobi=1,
+                                     restart=30) as bt:
+                nsolve = 0
+                bt.solve()
+                nsolve += 1
+                evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(2)]
+                barrier()
+                stb = 0
+                for k in range(2):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                        evb[k][0].record(stream)
+                    stb = bt.solve()
+                    nsolve += 1
+                    with torch.cuda.stream(stream):
+                        evb[k][1].record(stream)
+                barrier()
+                tb = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in evb) / 1e3 / 2, "cuda")
+                infos = [bt.info(i) for i in range(len(probs))]
+                bs = bt.stats()
+                variants[f"batch64_{prec}"] = {
+                    "s": tb, "instances_per_s": len(probs) / tb, "status": stb,
+                    "converged": sum(1 for q, i_ in zip(probs, infos) if i_["status"] == 0 and i_["rel_res_comp"] < q.tau),
+                    "outer_steps_total": sum(i_["steps"] for i_ in infos),
+                    "inner_its_total": sum(i_["inner_its_A"] + i_["inner_its_B"] for i_ in infos),
+                    "ticks_per_solve": bs["ticks"], "launches_per_solve": bs["launches"],
+                    "algorithmic_GBps": bs["bytes"] / nsolve / tb / 1e9,
+                    "rows": sum((q.A.n + q.B.n) * q.r for q in probs)}
+    pool.shutdown()
+
+    # ---- roofline of the dominant kernel of the headline solve (HBM) ----
+    dom = max(SWEEPS, key=lambda k: stats[k][0])
     ms, by, fl, la = stats[dom]
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        with open(pk) as fh_:
-            peaks = json.load(fh_)
-    hbm = peaks.get("hbm_gbs") or 6800.0
-    ach_tf = (fl / la) / ((ms / la) * 1e-3) / 1e12 if ms > 0 else None
     ach_gb = (by / la) / ((ms / la) * 1e-3) / 1e9 if ms > 0 else None
-    total_ms = sum(v[0] for v in stats.values())
-    kern = {k: {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
-                "launches": v[3],
-                "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None,
-                "TFLOPs": round(v[2] / (v[0] * 1e-3) / 1e12, 4) if v[0] > 0 else None}
-            for k, v in stats.items()}
+    ratio = NCU_TRAFFIC_RATIO.get(dom)
     line = {
         "metric": METRIC, "value": t_solve, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 Krylov basis/sweeps + f64 outer" if a.precision == "fp32" else a.precision,
+        "data": "synthetic",
         "config": {"workload": a.workload, "n": n, "m": m, "r": r, "restart": rst,
                    "jacobi": bool(jac), "strategy": a.strategy, "tau": p.tau, "precision": a.precision,
-                   "kmax": a.kmax,
+                   "kmax": a.kmax, "driver": "host (per-kernel CUDA events on every 4th device iteration)",
                    "shifts": len(p.alpha), "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "flushed (512 MiB write) before every timed solve",
                    "outer_steps": info["steps"], "inner_its_A": info["inner_its_A"],
                    "inner_its_B": info["inner_its_B"], "rel_res_comp": info["rel_res_comp"],
-                   "status": st,
-                   "timing": "CUDA events on the solver stream; kernel events on every 4th device iteration"},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": ach_tf, "peak": FP64_NOMINAL_TFLOPS,
-                     "unit": "TFLOP/s", "frac": (ach_tf / FP64_NOMINAL_TFLOPS) if ach_tf else None,
-                     "peak_source": "nominal FP64 rate of the recipe (GB300 has ~2 DFMA/clk/SM)",
-                     "traffic": None, "achieved_GBps": ach_gb, "hbm_peak_GBps": hbm,
-                     "hbm_frac": (ach_gb / hbm) if ach_gb else None},
-        "kernels": kern,
+                   "status": st, "device_bytes_of_solver": footprint},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach_gb, "peak": hbm, "unit": "GB/s",
+                     "frac": (ach_gb / hbm) if ach_gb else None, "peak_source": hbm_src,
+                     "traffic": (ratio * by / la) if ratio else None,
+                     "sweeps_GBps": main_sum["spmm_orth_GBps"],
+                     "sweeps_frac": (main_sum["spmm_orth_GBps"] / hbm) if main_sum["spmm_orth_GBps"] else None},
+        "kernels": kernel_table(stats),
         "variants": variants,
         "gpu_launches": info["launches"] * a.steps,
         "clocks": clocks,

@@ -94,7 +94,16 @@ typedef struct sylv_opts {
                                     the kernels set (no host round trip inside a solve);
                                     1: the host launches every device iteration.  Profiling
                                     (sylv_adi_profile) always uses the host-driven loop. */
+    int32_t ortho;               /* Arnoldi orthogonalisation of the inner GMRES:
+                                    SYLV_ORTHO_CGS2: classical Gram-Schmidt twice, three
+                                    sweeps over the basis and three reductions per step;
+                                    SYLV_ORTHO_DCGS2: the second pass delayed into the next
+                                    step (Swirydowicz et al., Numer. Linear Algebra Appl. 28,
+                                    2021): two sweeps, one reduction per step */
 } sylv_opts;
+
+#define SYLV_ORTHO_CGS2  0
+#define SYLV_ORTHO_DCGS2 1
 
 #define SYLV_MAX_RESTART 30
 #define SYLV_MAX_RANK    4

@@ -14,9 +14,12 @@ y = t_{k-1}(:, l).  The paper's guidance for the inner solver (Sec. 3.3,
 
 The paper uses BiCGstab/MINRES in its experiments; restarted GMRES is the
 textbook method of Saad and Schultz (1986) with Givens rotations for the
-Hessenberg least-squares problem.  Orthogonalisation is either modified
-Gram-Schmidt or classical Gram-Schmidt applied twice (CGS2); both are
-written out plainly below.  Initial guess x0 = 0 (the paper is silent).
+Hessenberg least-squares problem.  Orthogonalisation is modified
+Gram-Schmidt, classical Gram-Schmidt applied twice (CGS2), or CGS2 with the
+second pass delayed by one step (DCGS2, Swirydowicz, Langou, Ananthan, Yang
+and Thomas, Numer. Linear Algebra Appl. 28 (2021); Bielich et al., Parallel
+Comput. 112 (2022)); all are written out plainly below.  Initial guess
+x0 = 0 (the paper is silent).
 """
 from __future__ import annotations
 
@@ -68,6 +71,54 @@ def cgs2_step(V, w):
     return h1 + h2, w
 
 
+def arnoldi_dcgs2(apply, v0, k):
+    """k Arnoldi steps with delayed reorthogonalisation, starting from the
+    unit vector v0; returns (V, H) with V (k+1) x n orthonormal rows and H
+    the (k+1) x k Hessenberg matrix of apply(V[:k].T) = V.T @ H, plus the
+    number of operator applications.
+
+    Step j works on u_j, the once-orthogonalised candidate for v_j (u_0 = v0):
+      y = apply(u_j)                         (the product of step j)
+      s = V_<j^* u_j,  alpha = u_j^* u_j      (the delayed second pass)
+      z = V_<j^* y,    gamma = u_j^* y        (first pass of the next column)
+      beta = sqrt(alpha - |s|^2)              (norm of u_j - V_<j s)
+      column j-1 of H = (first-pass coefficients) + s, H[j, j-1] = beta
+      v_j = (u_j - V_<j s) / beta
+      u_{j+1} = (y - V_<j z - v_j (v_j^* y)) / beta,  v_j^* y = (gamma - s^* z) / beta
+    and the first-pass coefficients of column j are V_<=j^* A v_j, which
+    follow from z, gamma, s and the columns of H so far because
+    A V_<j = V_<=j H (no further product):
+      h1 = ([z; v_j^* y] - H[:j+1, :j] s) / beta.
+    A product is skipped at the last step (its result is never used)."""
+    n = v0.shape[0]
+    dtype = v0.dtype
+    V = np.zeros((k + 1, n), dtype)
+    H = np.zeros((k + 1, k), dtype)
+    u = v0.copy()
+    h1 = None
+    napply = 0
+    for j in range(k + 1):
+        y = apply(u) if j < k else None
+        napply += y is not None
+        s = V[:j].conj() @ u
+        alpha = np.vdot(u, u).real
+        beta = np.sqrt(max(alpha - np.vdot(s, s).real, 0.0))
+        if j >= 1:
+            H[:j, j - 1] = h1 + s
+            H[j, j - 1] = beta
+        if beta == 0.0:
+            return V[:j], H[:j, :max(j - 1, 0)], napply
+        V[j] = (u - V[:j].T @ s) / beta
+        if j == k:
+            break
+        z = V[:j].conj() @ y
+        gamma = np.vdot(u, y)
+        vy = (gamma - np.vdot(s, z)) / beta
+        h1 = (np.concatenate([z, [vy]]) - H[:j + 1, :j] @ s) / beta
+        u = (y - V[:j].T @ z - V[j] * vy) / beta
+    return V, H, napply
+
+
 def shifted_apply(S, sigma, x):
     """(Op + sigma I) x."""
     return S @ x + sigma * x
@@ -93,6 +144,8 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
     if beta <= tol:
         return GmresResult(x, beta, 0, 0, True, hist)
     m = restart
+    if ortho == "dcgs2":
+        return _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype)
     while True:
         cycles += 1
         V = np.zeros((m + 1, n), dtype)
@@ -147,3 +200,76 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
             return GmresResult(x, beta, iters, cycles, True, hist)
         if iters >= max_iters:
             return GmresResult(x, beta, iters, cycles, False, hist)
+
+
+def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype) -> GmresResult:
+    """The restarted GMRES above with the Arnoldi steps of arnoldi_dcgs2.
+
+    Column j-1 of the Hessenberg matrix is complete once step j has the
+    delayed second-pass coefficients of u_j; its Givens update and the stop
+    test follow, so a cycle that stops there has already formed the product
+    of step j (unused).  Arnoldi steps are counted as completed columns."""
+    n = b.shape[0]
+    x = np.zeros(n, dtype)
+    r = b.copy()
+    beta0 = np.linalg.norm(r)
+    hist = []
+    iters = cycles = 0
+    if beta0 <= tol:
+        return GmresResult(x, beta0, 0, 0, True, hist)
+    while True:
+        cycles += 1
+        V = np.zeros((m + 1, n), dtype)
+        H = np.zeros((m + 1, m), dtype)     # Hessenberg columns as formed
+        R = np.zeros((m + 1, m), dtype)     # the same columns, rotated
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype)
+        g = np.zeros(m + 1, dtype)
+        g[0] = beta0
+        u = r / beta0
+        h1 = None
+        k = 0
+        for j in range(m + 1):
+            y = shifted_apply(S, sigma, pinv * u) if j < m else None
+            s = V[:j].conj() @ u
+            alpha = np.vdot(u, u).real
+            beta = np.sqrt(max(alpha - np.vdot(s, s).real, 0.0))
+            if j >= 1:
+                c_ = j - 1
+                H[:j, c_] = h1 + s
+                H[j, c_] = beta
+                h = H[: j + 1, c_].copy()
+                for i in range(c_):
+                    t0 = cs[i] * h[i] + sn[i] * h[i + 1]
+                    t1 = -np.conj(sn[i]) * h[i] + cs[i] * h[i + 1]
+                    h[i], h[i + 1] = t0, t1
+                c, sg = givens(h[c_], h[c_ + 1])
+                cs[c_], sn[c_] = c, sg
+                h[c_] = c * h[c_] + sg * h[c_ + 1]
+                h[c_ + 1] = 0.0
+                g[c_ + 1] = -np.conj(sg) * g[c_]
+                g[c_] = c * g[c_]
+                R[: j + 1, c_] = h
+                iters += 1
+                est = abs(g[c_ + 1])
+                hist.append(est)
+                k = j
+                if est <= tol or j == m or iters >= max_iters or beta == 0.0:
+                    break
+            V[j] = (u - V[:j].T @ s) / beta
+            z = V[:j].conj() @ y
+            gamma = np.vdot(u, y)
+            vy = (gamma - np.vdot(s, z)) / beta
+            h1 = (np.concatenate([z, [vy]]) - H[: j + 1, :j] @ s) / beta
+            u = (y - V[:j].T @ z - V[j] * vy) / beta
+        y_ = np.zeros(k, dtype)
+        for i in range(k - 1, -1, -1):
+            acc = g[i] - R[i, i + 1: k] @ y_[i + 1: k]
+            y_[i] = acc / R[i, i] if R[i, i] != 0 else 0.0
+        x = x + pinv * (V[:k].T @ y_)
+        r = b - shifted_apply(S, sigma, x)
+        beta0 = np.linalg.norm(r)
+        if beta0 <= tol:
+            return GmresResult(x, beta0, iters, cycles, True, hist)
+        if iters >= max_iters:
+            return GmresResult(x, beta0, iters, cycles, False, hist)

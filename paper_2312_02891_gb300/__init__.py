@@ -33,6 +33,7 @@ ERRORS = {-1: "INVALID", -2: "CUDA", -3: "NOMEM", -4: "MAXIT", -5: "INNER_STALL"
 WARNINGS = (-4, -5)      # solve finished, factors valid
 STRATEGIES = {"fixed": 0, "nobl_mid": 1, "bl_mid": 2, "nobl_A": 3, "bl_A": 4, "nobl_B": 5, "bl_B": 6}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+ORTHO = {"cgs2": 0, "dcgs2": 1}
 HIST_COLUMNS = ("k", "alpha", "beta", "dA", "dB", "eps_hat", "nrA", "nrB", "itsA", "itsB",
                 "u", "v", "res_comp", "N_w")
 EXPORTED = (
@@ -69,7 +70,8 @@ class SylvOpts(C.Structure):
                 ("dmax_A", C.c_double), ("dmax_B", C.c_double), ("kmax", C.c_int32),
                 ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
-                ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32)]
+                ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32),
+                ("ortho", C.c_int32)]
 
 
 class SylvProblem(C.Structure):
@@ -192,6 +194,8 @@ def sylv_opts_default(**overrides) -> SylvOpts:
             v = STRATEGIES[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "ortho" and isinstance(v, str):
+            v = ORTHO[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)

@@ -66,6 +66,10 @@ static int resolve_opts(const sylv_opts* opts, double tol, sylv_opts* o) {
         set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
         return SYLV_ERR_INVALID;
     }
+    if (o->ortho != SYLV_ORTHO_CGS2 && o->ortho != SYLV_ORTHO_DCGS2) {
+        set_error("unknown orthogonalisation %d", o->ortho);
+        return SYLV_ERR_INVALID;
+    }
     if (o->precision < SYLV_PREC_FP64 || o->precision > SYLV_PREC_BF16) {
         set_error("precision %d not built", o->precision);
         return SYLV_ERR_UNSUPPORTED;
@@ -93,6 +97,7 @@ int sylv_opts_default(sylv_opts* o) {
     o->bl_clamp = 0;
     o->rows_per_chunk = 0;
     o->driver = 1;
+    o->ortho = SYLV_ORTHO_CGS2;
     return SYLV_OK;
 }
 

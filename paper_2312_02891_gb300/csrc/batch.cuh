@@ -166,6 +166,7 @@ struct Batch : BatchBase {
             }
         }
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, o.restart, rpc, stream));
+        eng.ortho = o.ortho;
         SYLV_TRY(st.alloc(count));
         SYLV_CK(cudaMemset(st.p, 0, (size_t)count * sizeof(AdiState<T>)));
         // ---- per-instance descriptors and the outer-kernel work list ----
@@ -215,11 +216,13 @@ struct Batch : BatchBase {
         return SYLV_OK;
     }
 
-    int add_kernel(cudaGraphNode_t* node, cudaGraph_t g, cudaGraphNode_t* dep, void* func, int grid, void** args) {
+    int add_kernel(cudaGraphNode_t* node, cudaGraph_t g, cudaGraphNode_t* dep, void* func, int grid, void** args,
+                   int smem = 0) {
         cudaKernelNodeParams kp = {};
         kp.func = func;
         kp.gridDim = dim3(grid);
         kp.blockDim = dim3(SYLV_BLOCK);
+        kp.sharedMemBytes = smem;
         kp.kernelParams = args;
         SYLV_CK(cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp));
         return SYLV_OK;
@@ -263,9 +266,15 @@ struct Batch : BatchBase {
         cudaGraphNode_t n_o, n_s, n1, n2, n3, n_if, n4, n5;
         SYLV_TRY(add_kernel(&n_o, body, nullptr, (void*)k_batch_outer<T, S, C>, nbitems, ao));
         SYLV_TRY(add_kernel(&n_s, body, &n_o, (void*)k_batch_step<T, S, C>, nbitems, ao));
-        SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_arnoldi_spmv<T, S, C>, ni, a1));
-        SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, a2));
-        SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, a3));
+        const int sm = sweep_smem_bytes<S, C>();
+        if (eng.ortho == 1) {
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, sm));
+            SYLV_TRY(add_kernel(&n3, body, &n1, (void*)k_dcgs_b<T, S, C>, ni, a2, sm));
+        } else {
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_arnoldi_spmv<T, S, C>, ni, a1, sm));
+            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, a2, sm));
+            SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, a3, sm));
+        }
         cudaGraphNodeParams ip = {};
         ip.type = cudaGraphNodeTypeConditional;
         ip.conditional.handle = h_restart;

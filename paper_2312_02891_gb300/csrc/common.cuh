@@ -268,6 +268,14 @@ struct SysState {
     T sn[SYLV_MR];
     T g[SYLV_MAXV];
     T y[SYLV_MR];                // scale-folded least-squares solution
+    // delayed CGS2 (DCGS2): Hessenberg columns as formed (unrotated),
+    // coefficients of the pending update sweep and its step
+    T Hr[SYLV_MR * SYLV_MAXV];
+    T cz[SYLV_MAXV];
+    T cv;
+    double sjb;
+    int jb;
+    int upd;
 };
 
 // Work item of a launch: (system, chunk).
@@ -307,11 +315,16 @@ template <> struct FmaFlops<cflt> { static constexpr double v = 8.0; };
 
 // Chunk 0 of each system adds the system's algorithmic bytes and
 // multiply-adds (converted to flops by the caller's type) for this launch.
-__device__ __forceinline__ void count_work(BatchCtl* ctl, int kid, int chunk, double bytes, double flops) {
-    if (chunk == 0 && threadIdx.x == 0 && ctl) {
-        atomicAdd(&ctl->bytes[kid], bytes);
-        atomicAdd(&ctl->flops[kid], flops);
-    }
-}
+// Algorithmic bytes and flops of a launch, added once per system (chunk 0,
+// thread 0).  A macro, so that the float64 expressions are evaluated only by
+// that thread: in the 32-bit kernels every thread evaluating them kept this
+// GPU's small float64 pipe busy at the start of every block.
+#define count_work(ctl, kid, chunk, BYTES, FLOPS)                  \
+    do {                                                           \
+        if ((chunk) == 0 && threadIdx.x == 0 && (ctl)) {           \
+            atomicAdd(&(ctl)->bytes[kid], (double)(BYTES));        \
+            atomicAdd(&(ctl)->flops[kid], (double)(FLOPS));        \
+        }                                                          \
+    } while (0)
 
 }  // namespace sylv

@@ -36,6 +36,21 @@ template <typename T> struct Dev {
 
 inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
 
+// The staged sweeps take more than the default 48 KB of dynamic shared
+// memory: allow it once per instantiation (the attribute is per device, so
+// it is set again on the device current at each call; it is cheap).
+template <typename T, typename S, typename C>
+int sweep_kernel_setup() {
+    const int b = sweep_smem_bytes<S, C>();
+    if (b <= 48 * 1024) return SYLV_OK;
+    SYLV_CK(cudaFuncSetAttribute(k_arnoldi_spmv<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    SYLV_CK(cudaFuncSetAttribute(k_cgs_pass2<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    SYLV_CK(cudaFuncSetAttribute(k_cgs_pass3<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    SYLV_CK(cudaFuncSetAttribute(k_dcgs_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    SYLV_CK(cudaFuncSetAttribute(k_dcgs_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    return SYLV_OK;
+}
+
 // Rows per work item of the basis sweeps, in whole 32-row tiles, at least
 // 256 rows: one wave of resident blocks over all rows of the batch for the
 // 32-bit sweeps (several resident blocks per SM hide each other's fixed
@@ -44,7 +59,9 @@ inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
 template <typename T, typename S, typename C>
 int sweep_rows_per_chunk(long long total_rows) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_pass2<T, S, C>, SYLV_BLOCK, 0) != cudaSuccess ||
+    if (sweep_kernel_setup<T, S, C>() != SYLV_OK ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_pass2<T, S, C>, SYLV_BLOCK,
+                                                      sweep_smem_bytes<S, C>()) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const long long waves = SweepOcc<C>::value > 1 ? 1 : 2;
@@ -80,6 +97,8 @@ struct Engine {
     int profile = 0;
     cudaEvent_t pev[4][6] = {};
     int pending[4] = {0, 0, 0, 0};
+    int pkid[4][5] = {};                // kernel id of each timed interval
+    int ortho = 0;                      // 0: CGS2 (three sweeps), 1: delayed CGS2 (two sweeps)
     double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
     long long samples[K_COUNT] = {};    // sampled launches
     long long launches[K_COUNT] = {};   // all launches
@@ -105,6 +124,7 @@ struct Engine {
         stream = s;
         restart = restart_;
         nsys = (int)sys_n.size();
+        SYLV_TRY((sweep_kernel_setup<T, S, C>()));
         long long total_rows = 0;
         for (int q = 0; q < nsys; ++q) total_rows += sys_n[q];
         if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(total_rows);
@@ -172,21 +192,36 @@ struct Engine {
         const dim3 grid(nitems), block(SYLV_BLOCK);
         cudaEvent_t* pe = (profile && (tick_no++ % prof_every) == 0) ? pev[slot] : nullptr;
         if (pe) SYLV_CK(cudaEventRecord(pe[0], stream));
-        k_arnoldi_spmv<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p, cgs_mode);
-        if (pe) SYLV_CK(cudaEventRecord(pe[1], stream));
-        k_cgs_pass2<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
-        if (pe) SYLV_CK(cudaEventRecord(pe[2], stream));
-        k_cgs_pass3<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
-        if (pe) SYLV_CK(cudaEventRecord(pe[3], stream));
-        launches[K_SPMV]++; launches[K_CGS2]++; launches[K_CGS3]++;
+        const int sm = sweep_smem_bytes<S, C>();
+        int nk = 0;
+        auto mark = [&](int kid) -> int {
+            if (pe) {
+                pkid[slot][nk] = kid;
+                SYLV_CK(cudaEventRecord(pe[++nk], stream));
+            }
+            launches[kid]++;
+            return SYLV_OK;
+        };
+        if (ortho == 1 && cgs_mode == 0) {
+            k_dcgs_a<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            SYLV_TRY(mark(K_SPMV));
+            k_dcgs_b<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            SYLV_TRY(mark(K_CGS3));
+        } else {
+            k_arnoldi_spmv<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p, cgs_mode);
+            SYLV_TRY(mark(K_SPMV));
+            k_cgs_pass2<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            SYLV_TRY(mark(K_CGS2));
+            k_cgs_pass3<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
+            SYLV_TRY(mark(K_CGS3));
+        }
         if (cgs_mode == 0) {
             k_restart_update<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
-            if (pe) SYLV_CK(cudaEventRecord(pe[4], stream));
+            SYLV_TRY(mark(K_RUPD));
             k_restart_residual<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
-            if (pe) SYLV_CK(cudaEventRecord(pe[5], stream));
-            launches[K_RUPD]++; launches[K_RRES]++;
+            SYLV_TRY(mark(K_RRES));
         }
-        if (pe) pending[slot] = cgs_mode == 0 ? 5 : 3;
+        if (pe) pending[slot] = nk;
         SYLV_CK(cudaGetLastError());
         return SYLV_OK;
     }
@@ -196,8 +231,8 @@ struct Engine {
         for (int q = 0; q < pending[slot]; ++q) {
             float ms = 0.f;
             SYLV_CK(cudaEventElapsedTime(&ms, pev[slot][q], pev[slot][q + 1]));
-            kernel_ms[q] += ms;
-            samples[q] += 1;
+            kernel_ms[pkid[slot][q]] += ms;
+            samples[pkid[slot][q]] += 1;
         }
         pending[slot] = 0;
         return SYLV_OK;
@@ -531,6 +566,7 @@ struct Adi : AdiBase {
         d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
         d.s = st.p; d.h_done = d_hdone;
         graph_on = a.o.driver == 0 ? 1 : 0;
+        eng.ortho = a.o.ortho;
         return SYLV_OK;
     }
 
@@ -571,12 +607,12 @@ struct Adi : AdiBase {
     int h_one = 1, h_zero = 0;
 
     int add_kernel(cudaGraphNode_t* node, cudaGraph_t g, cudaGraphNode_t* dep, void* func, int grid,
-                   int block, void** args) {
+                   int block, void** args, int smem = 0) {
         cudaKernelNodeParams kp = {};
         kp.func = func;
         kp.gridDim = dim3(grid);
         kp.blockDim = dim3(block);
-        kp.sharedMemBytes = 0;
+        kp.sharedMemBytes = smem;
         kp.kernelParams = args;
         kp.extra = nullptr;
         SYLV_CK(cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp));
@@ -629,9 +665,15 @@ struct Adi : AdiBase {
         void* a3[] = {&sdp, &stp, &itp, &ctp, &mode0};
         void* a4[] = {&sdp, &stp, &itp, &ctp};
         void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
-        SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_arnoldi_spmv<T, S, C>, ni, SYLV_BLOCK, a1));
-        SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, SYLV_BLOCK, a2));
-        SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, SYLV_BLOCK, a3));
+        const int sm = sweep_smem_bytes<S, C>();
+        if (eng.ortho == 1) {
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5, sm));
+            SYLV_TRY(add_kernel(&n3, loop_body, &n1, (void*)k_dcgs_b<T, S, C>, ni, SYLV_BLOCK, a2, sm));
+        } else {
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_arnoldi_spmv<T, S, C>, ni, SYLV_BLOCK, a1, sm));
+            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, SYLV_BLOCK, a2, sm));
+            SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, SYLV_BLOCK, a3, sm));
+        }
         SYLV_TRY(add_cond(&n_if, loop_body, &n3, h_restart, cudaGraphCondTypeIf, &if_body));
         SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, ni, SYLV_BLOCK, a4));
         SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, ni, SYLV_BLOCK, a5));

@@ -24,7 +24,7 @@
 
 namespace sylv {
 
-constexpr int PSTRIDE = SYLV_MAXV + 1;     // partial-sum slots per chunk
+constexpr int PSTRIDE = 2 * SYLV_MAXV + 2; // partial-sum slots per chunk (delayed CGS2: 2j + 2 sums)
 
 // Per-thread accumulators (type A) -> block sums in type T written to out[0..cnt).
 template <typename T, typename A, int NV>
@@ -141,6 +141,75 @@ __device__ __forceinline__ void block_reduce_to(A (&acc)[NV], int cnt, T* out, T
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged sweeps (real 32-bit and 16-bit basis storage).  Each warp streams
+// its row tiles of the block's chunk (tiles t0 + warp, t0 + warp + NWARP, ...)
+// through a ring of shared-memory stages: the tile's vectors 0..nv-1 (one
+// contiguous range in the tile-major basis) and its 32 rows of the work
+// vector are copied with cp.async, NST - 1 tiles ahead of use.  No register
+// holds an in-flight basis value, so the accumulators alone set the register
+// count, and every warp keeps several KB of loads in flight.
+// ---------------------------------------------------------------------------
+constexpr int SWEEP_WARP_SMEM = 8192;                         // staging bytes per warp
+constexpr int SWEEP_SMEM = SWEEP_WARP_SMEM * SYLV_NWARP;      // dynamic shared memory per block
+
+template <typename S, typename C> struct Staged {
+    static constexpr bool value = sizeof(S) <= 4 && sizeof(C) == 4;   // real float32 / bfloat16 basis
+};
+template <typename S, typename C> constexpr int sweep_smem_bytes() { return Staged<S, C>::value ? SWEEP_SMEM : 0; }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+// Runs body(i, sv, wv) for every row i < r1 of the warp's tiles in [t0, t1),
+// with sv[32 l] = V_l(i) (l < nv) and wv = w(i) read from the stage.
+template <int NV, typename S, typename C, typename Body>
+__device__ __forceinline__ void stream_tiles(const S* __restrict__ V, size_t tstride, const C* __restrict__ w,
+                                             int t0, int t1, int r1, int nv, Body body) {
+    extern __shared__ __align__(16) unsigned char sweep_dsm[];
+    constexpr int NVS = NV < SYLV_MAXV ? NV : SYLV_MAXV;               // vectors a stage must hold
+    constexpr int VB = NVS * 32 * (int)sizeof(S);                       // basis bytes of a tile
+    constexpr int TB = VB + 32 * (int)sizeof(C);                        // + the work vector rows
+    constexpr int NST0 = SWEEP_WARP_SMEM / TB;
+    constexpr int NST = NST0 > 8 ? 8 : NST0;
+    static_assert(NST >= 2, "a warp needs two stages");
+    constexpr int P = NST - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wsm = sweep_dsm + warp * SWEEP_WARP_SMEM;
+    const int ntile = t1 - t0;
+    const int mine = ntile > warp ? (ntile - warp + SYLV_NWARP - 1) / SYLV_NWARP : 0;
+    const int vchunks = nv * 32 * (int)sizeof(S) / 16;
+    constexpr int WCH = 32 * (int)sizeof(C) / 16;
+    auto issue = [&](int q) {
+        const size_t t = (size_t)(t0 + warp + q * SYLV_NWARP);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(V + t * tstride);
+        unsigned char* dst = wsm + (q % NST) * TB;
+        for (int c = lane; c < vchunks; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
+        if (lane < WCH) cp_async16(dst + VB + 16 * lane, reinterpret_cast<const unsigned char*>(w + t * 32) + 16 * lane);
+    };
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        if (q < mine) issue(q);
+        cp_async_commit();
+    }
+    for (int q = 0; q < mine; ++q) {
+        if (q + P < mine) issue(q + P);
+        cp_async_commit();
+        cp_async_wait<P>();
+        __syncwarp();
+        const unsigned char* st = wsm + (q % NST) * TB;
+        const int i = (t0 + warp + q * SYLV_NWARP) * 32 + lane;
+        if (i < r1) body(i, reinterpret_cast<const S*>(st) + lane, reinterpret_cast<const C*>(st + VB)[lane]);
+        __syncwarp();
+    }
+}
+
 // Row i of w = (Op + sigma I) P^{-1} (sj * V_j): the pre-scaled stencil
 // diagonals in C precision, or the generic operator row in float64.
 template <int LAY, typename T, typename S, typename C>
@@ -199,11 +268,28 @@ __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDe
             for (int l = 0; l < NV; ++l)
                 if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), wi);
         }
+    } else if constexpr (Staged<S, C>::value && LAY == 1) {
+        // 32-bit and 16-bit real bases: the product rows first, in the
+        // warp-tile order of the staged sweep (each warp then stages only
+        // rows it wrote itself), then the dot products from shared memory
+        if (mode == 0) {
+            const int lane = threadIdx.x & 31;
+            for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
+                const int i = t * 32 + lane;
+                if (i < r1) w[i] = spmv_row<LAY>(sd, op, st, vj, sj, i);
+            }
+            __syncwarp();
+        }
+        stream_tiles<NV, S, C>(V, sd.tstride, w, r0 >> 5, (r1 + 31) >> 5, r1, j + 1,
+                               [&](int, const S* sv, C wv) {
+#pragma unroll
+                                   for (int l = 0; l < NV; ++l)
+                                       if (l <= j) acc[l] += cmul(cvt<C>(sv[32 * l]), wv);
+                               });
     } else {
-        // 32-bit sweeps: the product rows first, then the dot products over
-        // the same rows (each thread re-reads only the w entries it wrote),
-        // so neither loop carries the other's registers and more warps stay
-        // resident
+        // other 32-bit sweeps: the product rows first, then the dot products
+        // over the same rows (each thread re-reads only the w entries it
+        // wrote), so neither loop carries the other's registers
         if (mode == 0)
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) w[i] = spmv_row<LAY>(sd, op, st, vj, sj, i);
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -267,15 +353,27 @@ __device__ __forceinline__ void pass2_rows(const SysDesc<T, S, C>& sd, const C* 
     C acc[NV];
 #pragma unroll
     for (int l = 0; l < NV; ++l) acc[l] = zero<C>();
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        C w1 = w[i];
-        const S* __restrict__ vr = V + BI::row(sd, i);
+    if constexpr (Staged<S, C>::value && LAY == 1) {
+        stream_tiles<NV, S, C>(V, sd.tstride, w, r0 >> 5, (r1 + 31) >> 5, r1, j + 1, [&](int, const S* sv, C wv) {
+            C w1 = wv;
 #pragma unroll
-        for (int l = 0; l < NV; ++l)
-            if (l <= j) w1 -= cc[l] * cvt<C>(vr[BI::vec(sd, l)]);
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) w1 -= cc[l] * cvt<C>(sv[32 * l]);
 #pragma unroll
-        for (int l = 0; l < NV; ++l)
-            if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), w1);
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) acc[l] += cmul(cvt<C>(sv[32 * l]), w1);
+        });
+    } else {
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            C w1 = w[i];
+            const S* __restrict__ vr = V + BI::row(sd, i);
+#pragma unroll
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) w1 -= cc[l] * cvt<C>(vr[BI::vec(sd, l)]);
+#pragma unroll
+            for (int l = 0; l < NV; ++l)
+                if (l <= j) acc[l] += cmul(cvt<C>(vr[BI::vec(sd, l)]), w1);
+        }
     }
     block_reduce_to<T, C, NV>(acc, j + 1, out, red);
 }
@@ -313,57 +411,57 @@ k_cgs_pass2(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__
     if (threadIdx.x == 0) st->counter = 0;
 }
 
-// Last block of sweep 3: Hessenberg column j, Givens update, stop test, and
-// at the end of a cycle the least-squares solution by back substitution.
-// The block stages the rotations and R in shared memory; one warp runs the
+// Column c of the Hessenberg matrix is complete: s_col[0..c] (shared
+// memory) and the subdiagonal hn.  Applies the previous rotations and a new
+// one, updates g and the residual estimate, counts the Arnoldi step and
+// decides whether the cycle ends (estimate below tol, restart length, step
+// cap, non-finite value); at the end of a cycle the least-squares solution
+// y is formed by back substitution and the system moves to the update
+// phase.  Returns the (block-uniform) end decision.  One warp runs the
 // sequential parts.
 template <typename T>
-__device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState<T>* st, double nrm2) {
-    __shared__ T s_col[SYLV_MAXV];
+__device__ int hess_column_finish(int restart, double* hist, int hist_cap, SysState<T>* st, int c, const T* s_col,
+                                  double hn) {
     __shared__ T s_sn[SYLV_MR];
     __shared__ double s_cs[SYLV_MR];
     __shared__ T s_R[SYLV_MR * SYLV_MAXV];
     __shared__ T s_g[SYLV_MAXV];
     __shared__ int s_end;
-    const int j = st->j;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        s_col[i] = st->h1[i] + st->h2[i];
+    for (int i = threadIdx.x; i <= c; i += blockDim.x) {
         s_g[i] = st->g[i];
-        if (i < j) { s_cs[i] = st->cs[i]; s_sn[i] = st->sn[i]; }
+        if (i < c) { s_cs[i] = st->cs[i]; s_sn[i] = st->sn[i]; }
     }
-    // R columns 0..j-1 (needed only when the cycle ends; loaded in parallel)
-    for (int q = threadIdx.x; q < j * SYLV_MAXV; q += blockDim.x) s_R[q] = st->R[q];
+    // R columns 0..c-1 (needed only when the cycle ends; loaded in parallel)
+    for (int q = threadIdx.x; q < c * SYLV_MAXV; q += blockDim.x) s_R[q] = st->R[q];
     __syncthreads();
-    const double hn = sqrt(nrm2);
     if (threadIdx.x == 0) {
         T col[SYLV_MAXV];
-        for (int i = 0; i <= j; ++i) col[i] = s_col[i];
-        col[j + 1] = make_scalar<T>(hn, 0.0);
-        st->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-        for (int i = 0; i < j; ++i) {
-            const double c = s_cs[i];
-            const T s = s_sn[i];
-            const T t0 = c * col[i] + s * col[i + 1];
-            const T t1 = c * col[i + 1] - conjg(s) * col[i];
+        for (int i = 0; i <= c; ++i) col[i] = s_col[i];
+        col[c + 1] = make_scalar<T>(hn, 0.0);
+        for (int i = 0; i < c; ++i) {
+            const double cc_ = s_cs[i];
+            const T sn_ = s_sn[i];
+            const T t0 = cc_ * col[i] + sn_ * col[i + 1];
+            const T t1 = cc_ * col[i + 1] - conjg(sn_) * col[i];
             col[i] = t0;
             col[i + 1] = t1;
         }
-        double c;
-        T s;
-        givens(col[j], col[j + 1], c, s);
-        st->cs[j] = c;
-        st->sn[j] = s;
-        col[j] = c * col[j] + s * col[j + 1];
-        const T gj = s_g[j];
-        const T gj1 = -(conjg(s) * gj);
-        st->g[j + 1] = gj1;
-        st->g[j] = c * gj;
-        s_g[j] = c * gj;
-        for (int i = 0; i <= j; ++i) {
-            st->R[j * SYLV_MAXV + i] = col[i];
-            s_R[j * SYLV_MAXV + i] = col[i];
+        double cr;
+        T sr;
+        givens(col[c], col[c + 1], cr, sr);
+        st->cs[c] = cr;
+        st->sn[c] = sr;
+        col[c] = cr * col[c] + sr * col[c + 1];
+        const T gc = s_g[c];
+        const T gc1 = -(conjg(sr) * gc);
+        st->g[c + 1] = gc1;
+        st->g[c] = cr * gc;
+        s_g[c] = cr * gc;
+        for (int i = 0; i <= c; ++i) {
+            st->R[c * SYLV_MAXV + i] = col[i];
+            s_R[c * SYLV_MAXV + i] = col[i];
         }
-        const double est = absv(gj1);
+        const double est = absv(gc1);
         st->est = est;
         st->iters += 1;
         if (hist && st->iters - 1 < hist_cap) hist[st->iters - 1] = est;
@@ -372,20 +470,20 @@ __device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState
             st->status = ST_NONFINITE;
             st->nvec = 0;
             st->phase = PH_UPDATE;
-            end = 0;
-        } else if (est <= st->tol || j + 1 >= restart || st->iters >= st->max_iters) {
-            st->nvec = j + 1;
+            end = 2;
+        } else if (est <= st->tol || c + 1 >= restart || st->iters >= st->max_iters || hn == 0.0) {
+            st->nvec = c + 1;
             end = 1;
         } else {
-            st->j = j + 1;
             end = 0;
         }
         s_end = end;
     }
     __syncthreads();
-    if (!s_end || threadIdx.x >= 32) return;
+    const int end = s_end;
+    if (end != 1 || threadIdx.x >= 32) return end;
     // back substitution R y = g by columns, one warp: lane l owns g[l]
-    const int k = j + 1;
+    const int k = c + 1;
     const int lane = threadIdx.x;
     T gl = lane < k ? s_g[lane] : zero<T>();
     T yl = zero<T>();
@@ -399,6 +497,21 @@ __device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState
     if (lane < k) st->y[lane] = st->scale[lane] * yl;
     __syncwarp();
     if (lane == 0) st->phase = PH_UPDATE;
+    return end;
+}
+
+// Last block of sweep 3 (CGS2): Hessenberg column j = h1 + h2 with
+// subdiagonal ||v_{j+1}||; the next step when the cycle goes on.
+template <typename T>
+__device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState<T>* st, double nrm2) {
+    __shared__ T s_col[SYLV_MAXV];
+    const int j = st->j;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = st->h1[i] + st->h2[i];
+    __syncthreads();
+    const double hn = sqrt(nrm2);
+    if (threadIdx.x == 0) st->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    const int end = hess_column_finish<T>(restart, hist, hist_cap, st, j, s_col, hn);
+    if (end == 0 && threadIdx.x == 0) st->j = j + 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -483,7 +596,22 @@ __device__ __forceinline__ void cgs_pass3_body(const SysDesc<T, S, C>* __restric
         vn[ri] = xs;                                                          \
         acc[0] += abs2(cvt<C>(xs));                                           \
     }
-    SYLV_BUCKET_SWITCH(j, SYLV_PASS3_CALL)
+#define SYLV_PASS3_STAGED(NV)                                                 \
+    stream_tiles<NV, S, C>(V, sd.tstride, w, r0 >> 5, (r1 + 31) >> 5, r1, j + 1,     \
+                           [&](int i, const S* sv, C wv) {                    \
+                               C x = wv;                                      \
+                               _Pragma("unroll") for (int l = 0; l < NV; ++l) \
+                                   if (l <= j) x -= cc[l] * cvt<C>(sv[32 * l]); \
+                               const S xs = cvt<S>(x);                        \
+                               vn[BI::row(sd, i)] = xs;                       \
+                               acc[0] += abs2(cvt<C>(xs));                    \
+                           });
+    if constexpr (Staged<S, C>::value && LAY == 1) {
+        SYLV_BUCKET_SWITCH(j, SYLV_PASS3_STAGED)
+    } else {
+        SYLV_BUCKET_SWITCH(j, SYLV_PASS3_CALL)
+    }
+#undef SYLV_PASS3_STAGED
 #undef SYLV_PASS3_CALL
     block_reduce_store<double, CR, 1>(acc, 1, reinterpret_cast<double*>(sd.part + (size_t)it.chunk * PSTRIDE));
     if (!last_block(&st->counter, sd.nchunks)) return;
@@ -511,6 +639,269 @@ __global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_cgs_pass3(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
             const Item* __restrict__ items, BatchCtl* ctl, int mode) {
     cgs_pass3_body<T, S, C, LAY>(sysd, sts, items, ctl, mode);
+    if (ctl->graph) graph_tail<T>(ctl, sts, K_CGS3);
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi with delayed reorthogonalisation (DCGS2; Swirydowicz et al.,
+// Numer. Linear Algebra Appl. 28 (2021)).  Step j works on u_j, the
+// once-orthogonalised candidate for v_j, stored (unnormalised, scale sj) in
+// basis slot j; slots 0..j-1 hold v_0..v_{j-1}.  Two sweeps per step:
+//   k_dcgs_a : y = (Op + sigma I) P^{-1} u_j and, in the same pass,
+//              s = V_<j^* u_j, alpha = u_j^* u_j, z = V_<j^* y, gamma = u_j^* y
+//              (one grid reduction).  Its last block sets beta = ||u_j - V s||
+//              = sqrt(alpha - |s|^2), completes Hessenberg column j-1 (first
+//              pass of the previous step + s, subdiagonal beta), runs the
+//              Givens update and stop test, and otherwise the coefficients of
+//              sweep b and the first pass of column j:
+//                h1 = ([z; v_j^* y] - H s) / beta,  v_j^* y = (gamma - s^* z) / beta
+//   k_dcgs_b : v_j = (u_j - V_<j s) / beta, u_{j+1} = (y - V_<j z - v_j v_j^* y) / beta
+//              (no reduction).
+// Relative to CGS2 (three sweeps, three reductions per step) one sweep and
+// two reductions go, for one extra product per restart cycle (the step that
+// completes the last column).
+// ---------------------------------------------------------------------------
+
+// Rows [r0, r1) of sweep a with NV >= j accumulators per kind.
+template <int NV, typename T, typename S, typename C>
+__device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const OpDesc& op, const SysState<T>* st,
+                                            int j, bool product, typename RealOf<C>::type sj, int r0, int r1,
+                                            T* out, T (*red)[PSTRIDE]) {
+    typedef BasisIx<1> BI;
+    const S* __restrict__ V = sd.V;
+    C* __restrict__ w = sd.w;
+    const S* __restrict__ uj = V + BI::vec(sd, j);
+    // acc[0..NV): X_l^* U, acc[NV..2NV): X_l^* Y, acc[2NV] = U^* U, acc[2NV+1] = U^* Y
+    C acc[2 * NV + 2];
+#pragma unroll
+    for (int l = 0; l < 2 * NV + 2; ++l) acc[l] = zero<C>();
+    auto body = [&](const C uv, const C wv, auto vl) {
+#pragma unroll
+        for (int l = 0; l < NV; ++l) {
+            if (l < j) {
+                const C xl = cvt<C>(vl(l));
+                acc[l] += cmul(xl, uv);
+                acc[NV + l] += cmul(xl, wv);
+            }
+        }
+        acc[2 * NV] += cmul(uv, uv);
+        acc[2 * NV + 1] += cmul(uv, wv);
+    };
+    if constexpr (Staged<S, C>::value) {
+        if (product) {
+            const int lane = threadIdx.x & 31;
+            for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
+                const int i = t * 32 + lane;
+                if (i < r1) w[i] = spmv_row<1>(sd, op, st, uj, sj, i);
+            }
+            __syncwarp();
+        }
+        stream_tiles<NV + 1, S, C>(V, sd.tstride, w, r0 >> 5, (r1 + 31) >> 5, r1, j + 1,
+                                   [&](int, const S* sv, C wv) {
+                                       const C uv = cvt<C>(sv[32 * j]);
+                                       body(uv, product ? wv : zero<C>(), [&](int l) { return sv[32 * l]; });
+                                   });
+    } else {
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            C wv = zero<C>();
+            if (product) {
+                wv = spmv_row<1>(sd, op, st, uj, sj, i);
+                w[i] = wv;
+            }
+            const S* __restrict__ vr = V + BI::row(sd, i);
+            body(cvt<C>(vr[BI::vec(sd, j)]), wv, [&](int l) { return vr[BI::vec(sd, l)]; });
+        }
+    }
+    // compact the used sums: s (j), z (j), alpha, gamma at 0..2j+1
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 2 * NV + 2; ++q) {
+        const int l = q < NV ? q : (q < 2 * NV ? q - NV : q - 2 * NV);
+        const int dst = q < NV ? l : (q < 2 * NV ? j + l : 2 * j + l);
+        const bool used = q < 2 * NV ? (l < j) : true;
+        if (used) {
+            const C v = warp_sum(acc[q]);
+            if (lane == 0) red[warp][dst] = cvt<T>(v);
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < 2 * j + 2; l += blockDim.x) {
+        T sum = zero<T>();
+#pragma unroll
+        for (int q = 0; q < SYLV_NWARP; ++q) sum += red[q][l];
+        out[l] = sum;
+    }
+}
+
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK, (SweepOcc<C>::value > 1 && sizeof(C) == 4) ? 2 : 1)
+k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
+         const Item* __restrict__ items, BatchCtl* ctl) {
+    typedef typename RealOf<C>::type CR;
+    __shared__ T red[SYLV_NWARP][PSTRIDE];
+    count_launch(ctl, K_SPMV);
+    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ctl->h_loop, 0u);
+    const Item it = items[blockIdx.x];
+    SysState<T>* st = sts + it.sys;
+    if (st->phase != PH_ARNOLDI) return;
+    const SysDesc<T, S, C> sd = sysd[it.sys];
+    const OpDesc op = ops[sd.op];
+    const int j = st->j;
+    const bool product = j < sd.restart;
+    const double sj = st->scale[j];
+    const int r0 = it.chunk * sd.rows_per_chunk;
+    const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
+    count_work(ctl, K_SPMV, it.chunk,
+               (product ? (double)op.nnz * sizeof(C) + (double)sd.n * (sizeof(S) + sizeof(C)) : 0.0) +
+                   (double)(j + 1) * sd.n * sizeof(S),
+               FmaFlops<C>::v * ((product ? (double)op.nnz : 0.0) + (2.0 * j + 2.0) * sd.n));
+    T* out = sd.part + (size_t)it.chunk * PSTRIDE;
+#define SYLV_DCGSA_CALL(NV) dcgs_a_rows<NV, T, S, C>(sd, op, st, j, product, (CR)sj, r0, r1, out, red)
+    if (j == 0) {
+        SYLV_DCGSA_CALL(4);
+    } else {
+        SYLV_BUCKET_SWITCH(j - 1, SYLV_DCGSA_CALL)
+    }
+#undef SYLV_DCGSA_CALL
+    if (!last_block(&st->counter, sd.nchunks)) return;
+    // ---- the step's sequential part: one block per system ----
+    __shared__ T tot[PSTRIDE];
+    __shared__ T s_s[SYLV_MAXV], s_z[SYLV_MAXV], s_col[SYLV_MAXV];
+    __shared__ double s_beta;
+    __shared__ T s_vy;
+    reduce_chunks(sd.part, sd.nchunks, PSTRIDE, 2 * j + 2, tot);
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        s_s[l] = (st->scale[l] * sj) * tot[l];
+        s_z[l] = st->scale[l] * tot[j + l];
+    }
+    if (threadIdx.x == 0) st->counter = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ss = 0.0;
+        for (int l = 0; l < j; ++l) ss += abs2(s_s[l]);
+        const double alpha = sj * sj * re(tot[2 * j]);
+        s_beta = sqrt(fmax(alpha - ss, 0.0));
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    int end = 0;
+    if (j >= 1) {
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            s_col[i] = st->h1[i] + s_s[i];
+            st->Hr[(j - 1) * SYLV_MAXV + i] = s_col[i];
+        }
+        if (threadIdx.x == 0) st->Hr[(j - 1) * SYLV_MAXV + j] = make_scalar<T>(beta, 0.0);
+        __syncthreads();
+        end = hess_column_finish<T>(sd.restart, sd.hist, sd.hist_cap, st, j - 1, s_col, beta);
+    } else if (!(beta > 0.0) || !isfinite(beta)) {
+        if (threadIdx.x == 0) {
+            if (!isfinite(beta)) st->status = ST_NONFINITE;
+            st->nvec = 0;
+            st->phase = PH_UPDATE;
+        }
+        end = 2;
+    }
+    if (end != 0) {
+        if (threadIdx.x == 0) st->upd = 0;
+        return;
+    }
+    // the cycle goes on: first pass of column j and the coefficients of sweep b
+    if (threadIdx.x == 0) {
+        T sz = zero<T>();
+        for (int l = 0; l < j; ++l) sz += conjg(s_s[l]) * s_z[l];
+        s_vy = sdiv((double)sj * tot[2 * j + 1] - sz, make_scalar<T>(beta, 0.0));
+    }
+    __syncthreads();
+    const double ib = 1.0 / beta;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        T hs = zero<T>();                        // (H s)_i over the first j columns
+        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += st->Hr[c * SYLV_MAXV + i] * s_s[c];
+        const T zi = i < j ? s_z[i] : s_vy;
+        st->h1[i] = ib * (zi - hs);
+    }
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        st->h2[l] = st->scale[l] * s_s[l];      // v_j   = sj U - sum h2_l X_l
+        st->cz[l] = st->scale[l] * s_z[l];      // u_j+1 = Y - sum cz_l X_l - cv X_j
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->cv = ib * s_vy;
+        st->sjb = sj;
+        st->jb = j;
+        st->upd = 1;
+        st->scale[j] = ib;
+        st->scale[j + 1] = ib;
+        st->j = j + 1;
+    }
+}
+
+// Rows [r0, r1) of sweep b: X_j <- sj U - sum_l a_l X_l, slot j+1 <- Y - sum_l c_l X_l - cv X_j.
+template <int NV, typename T, typename S, typename C>
+__device__ __forceinline__ void dcgs_b_rows(const SysDesc<T, S, C>& sd, int jb, C su, const C* ca, const C* cz, C cv,
+                                            int r0, int r1) {
+    typedef BasisIx<1> BI;
+    S* __restrict__ V = sd.V;
+    const C* __restrict__ w = sd.w;
+    auto body = [&](int i, const C uv, const C wv, auto vl) {
+        C xn = su * uv;
+        C un = wv;
+#pragma unroll
+        for (int l = 0; l < NV; ++l) {
+            if (l < jb) {
+                const C xl = cvt<C>(vl(l));
+                xn -= ca[l] * xl;
+                un -= cz[l] * xl;
+            }
+        }
+        const S xs = cvt<S>(xn);
+        un -= cv * cvt<C>(xs);
+        const size_t ri = BI::row(sd, i);
+        V[ri + BI::vec(sd, jb)] = xs;
+        V[ri + BI::vec(sd, jb + 1)] = cvt<S>(un);
+    };
+    if constexpr (Staged<S, C>::value) {
+        stream_tiles<NV + 1, S, C>(V, sd.tstride, w, r0 >> 5, (r1 + 31) >> 5, r1, jb + 1,
+                                   [&](int i, const S* sv, C wv) {
+                                       body(i, cvt<C>(sv[32 * jb]), wv, [&](int l) { return sv[32 * l]; });
+                                   });
+    } else {
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const S* __restrict__ vr = V + BI::row(sd, i);
+            body(i, cvt<C>(vr[BI::vec(sd, jb)]), w[i], [&](int l) { return vr[BI::vec(sd, l)]; });
+        }
+    }
+}
+
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
+k_dcgs_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const Item* __restrict__ items,
+         BatchCtl* ctl) {
+    count_launch(ctl, K_CGS3);
+    const Item it = items[blockIdx.x];
+    SysState<T>* st = sts + it.sys;
+    if (st->phase == PH_ARNOLDI && st->upd) {
+        const SysDesc<T, S, C> sd = sysd[it.sys];
+        const int jb = st->jb;
+        __shared__ C ca[SYLV_MAXV], cz[SYLV_MAXV];
+        for (int l = threadIdx.x; l < jb; l += blockDim.x) {
+            ca[l] = cvt<C>(st->h2[l]);
+            cz[l] = cvt<C>(st->cz[l]);
+        }
+        const C su = cvt<C>(make_scalar<T>(st->sjb, 0.0));
+        const C cv = cvt<C>(st->cv);
+        count_work(ctl, K_CGS3, it.chunk, (double)(jb + 1) * sd.n * sizeof(S) + (double)sd.n * (sizeof(C) + 2 * sizeof(S)),
+                   FmaFlops<C>::v * (2.0 * jb + 2.0) * sd.n);
+        __syncthreads();
+        const int r0 = it.chunk * sd.rows_per_chunk;
+        const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
+#define SYLV_DCGSB_CALL(NV) dcgs_b_rows<NV, T, S, C>(sd, jb, su, ca, cz, cv, r0, r1)
+        if (jb == 0) {
+            SYLV_DCGSB_CALL(4);
+        } else {
+            SYLV_BUCKET_SWITCH(jb - 1, SYLV_DCGSB_CALL)
+        }
+#undef SYLV_DCGSB_CALL
+    }
     if (ctl->graph) graph_tail<T>(ctl, sts, K_CGS3);
 }
 
@@ -604,6 +995,7 @@ __device__ __forceinline__ void restart_residual_body(const SysDesc<T, S, C>* __
         } else {
             st->cycles += 1;
             st->j = 0;
+            st->upd = 0;
             st->g[0] = make_scalar<T>(rn, 0.0);
             for (int l = 1; l < SYLV_MAXV; ++l) st->g[l] = zero<T>();
             st->scale[0] = 1.0 / rn;

@@ -33,7 +33,7 @@ def run_gpu(p, **opts):
 def compare(p, strategy, jacobi, xtol=1e-6, **extra):
     st, info, hist, Z, Y, gam = run_gpu(p, strategy=strategy, jacobi=int(jacobi), **extra)
     ref = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy=strategy, jacobi=jacobi,
-                **{k: v for k, v in extra.items() if k in ("kmax", "xi", "fixed_tol", "max_inner", "restart")})
+                **{k: v for k, v in extra.items() if k in ("kmax", "xi", "fixed_tol", "max_inner", "restart", "ortho")})
     A, B = p.A.to_scipy(), p.B.to_scipy()
     nfg = lowrank_norm2(p.f, p.g)
     assert st == 0, P.sylv_last_error()
@@ -195,3 +195,47 @@ def test_graph_solve_respects_kmax_and_zero_rhs():
     with P.SylvesterADI(p.A, p.B, np.zeros_like(p.f), p.g, p.alpha, p.beta, p.tau, driver=0) as s:
         assert s.solve() == 0
         assert s.info()["steps"] == 0
+
+
+# ------------------------------------------------ delayed CGS2 orthogonalisation
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("name,strategy,jacobi", [("small2d", "nobl_mid", False), ("tiny2d", "bl_mid", True)])
+def test_dcgs2_parity(precision, name, strategy, jacobi):
+    """GMRES with the second Gram-Schmidt pass delayed by one step (two
+    sweeps per Arnoldi step) against the oracle running the same
+    orthogonalisation: float64 to rounding (history within 1e-3), mixed
+    precision within the inner tolerances."""
+    compare(problem(name), strategy, jacobi, precision=precision, ortho="dcgs2")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dcgs2_complex_pairs(precision):
+    p = W.make_problem("cplx", 14, 2, "rot2", 60.0, 12, 2, "rot2", 40.0, 2, 33, 8, real_shifts=False)
+    info, ref, tr_gpu, tr_ref, dX = compare(p, "nobl_mid", True, precision=precision, ortho="dcgs2")
+    assert info["is_complex"] == 1
+
+
+def test_dcgs2_and_cgs2_agree():
+    """Both orthogonalisations build the same Krylov bases in exact
+    arithmetic: same outer and inner step counts, the same factored X."""
+    p = problem("small2d")
+    a = run_gpu(p, strategy="nobl_mid", jacobi=0, ortho="cgs2")
+    b = run_gpu(p, strategy="nobl_mid", jacobi=0, ortho="dcgs2")
+    assert a[0] == b[0] == 0 and a[1]["steps"] == b[1]["steps"]
+    assert abs(a[1]["inner_its_A"] - b[1]["inner_its_A"]) <= 2 and abs(a[1]["inner_its_B"] - b[1]["inner_its_B"]) <= 2
+    dX = factored_diff_fro(a[3], a[5], a[4], b[3], b[5], b[4]) / factored_fro(a[3], a[5], a[4])
+    assert dX <= 1e-7, dX
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dcgs2_graph_and_host_agree_bitwise(precision):
+    p = problem("tiny2d")
+    out = []
+    for driver in (0, 1):
+        st, info, hist, Z, Y, gam = run_gpu(p, strategy="nobl_mid", jacobi=1, precision=precision,
+                                            driver=driver, ortho="dcgs2")
+        assert st == 0
+        out.append((info["steps"], Z, Y, gam))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][3], out[1][3])

@@ -38,11 +38,11 @@ def check_instance(p, info, Z, Y, gam, xtol=1e-6, mixed=False):
     return ref
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_matches_oracle_per_instance(precision):
+@pytest.mark.parametrize("precision,ortho", [("fp64", "cgs2"), ("fp32", "cgs2"), ("fp32", "dcgs2")])
+def test_batch_matches_oracle_per_instance(precision, ortho):
     probs = small_batch(6)
     assert len({(p.A.n, p.B.n, p.f.shape[1]) for p in probs}) > 1    # uneven sizes and ranks
-    with P.SylvesterADIBatch(probs, precision=precision, **OPTS) as b:
+    with P.SylvesterADIBatch(probs, precision=precision, ortho=ortho, **OPTS) as b:
         st = b.solve()
         assert st == 0, P.sylv_last_error()
         for i, p in enumerate(probs):

@@ -19,7 +19,7 @@ import scipy.sparse.linalg as spla
 from paper_2312_02891_gb300 import workloads as W
 from oracle import controller as ctl
 from oracle.dense import bartels_stewart, dense_residual, kron_solve
-from oracle.gmres import cgs2_step, gmres, mgs_step
+from oracle.gmres import arnoldi_dcgs2, cgs2_step, gmres, mgs_step
 from oracle.lradi import lradi
 from oracle.residual import (block_norm2, factored_diff_fro, factored_fro, lowrank_fro,
                              lowrank_norm2, true_residual_norm2)
@@ -395,3 +395,49 @@ def test_convdiff_operator_structure():
     C = W.convdiff(8, 3, "zxy", 30.0).to_scipy().toarray()
     assert np.all(np.linalg.eigvals(C).real < 0)
     assert W.convdiff(8, 3, "zxy", 30.0).nnz == 7 * 512 - 6 * 64
+
+
+# ------------------------------------------------------ delayed CGS2 (DCGS2)
+
+@pytest.mark.parametrize("sigma", [0.0, -3.0 + 7.0j])
+def test_dcgs2_arnoldi_relation_and_orthonormality(sigma):
+    """The delayed second pass and the recovered first-pass coefficients give
+    an Arnoldi decomposition: Op V_k = V_{k+1} H_k with V orthonormal, to
+    rounding, on a nonsymmetric operator (real and complex shift)."""
+    A = W.convdiff(9, 2, "rot2", 40.0).to_scipy()
+    op = lambda x: A @ x + sigma * x
+    v0 = W.normal(3, 2, 0, A.shape[0]).astype(np.complex128 if sigma != 0 else np.float64)
+    v0 = v0 / np.linalg.norm(v0)
+    k = 30
+    V, H, napply = arnoldi_dcgs2(op, v0, k)
+    assert V.shape[0] == k + 1 and H.shape == (k + 1, k) and napply == k
+    nA = spla.norm(A) + abs(sigma)
+    AV = np.stack([op(V[i]) for i in range(k)])
+    assert np.abs(AV.T - V.T @ H).max() <= 1e-12 * nA
+    assert np.abs(V.conj() @ V.T - np.eye(k + 1)).max() <= 1e-12
+    assert np.all(np.abs(np.tril(H, -2)) == 0)        # Hessenberg
+    assert np.all(H[np.arange(1, k + 1), np.arange(k)].real > 0)
+
+
+def test_dcgs2_gmres_matches_cgs2_gmres(small):
+    """Same Krylov spaces in exact arithmetic: the delayed variant takes the
+    same number of steps and returns the same solution as CGS2 (small2d
+    A-side system, with and without Jacobi)."""
+    S = small.A.to_scipy()
+    for jac in (False, True):
+        a = gmres(S, small.beta[0], small.f[:, 0], 1e-10, 30, 3000, jac, "cgs2")
+        b = gmres(S, small.beta[0], small.f[:, 0], 1e-10, 30, 3000, jac, "dcgs2")
+        assert a.converged and b.converged and a.iters == b.iters and a.cycles == b.cycles
+        assert np.linalg.norm(a.x - b.x) <= 1e-12 * np.linalg.norm(a.x)
+        assert np.allclose(a.history, b.history, rtol=1e-6)
+
+
+def test_dcgs2_gmres_diagonal_operator_exact_steps():
+    """GMRES on a diagonal operator with d distinct entries converges in d
+    steps (minimal polynomial), also with the delayed orthogonalisation."""
+    d = np.repeat([-1.0, -2.0, -5.0, -9.0], 25)
+    S = sp.diags(d).tocsr()
+    b = W.normal(4, 1, 0, d.size)
+    res = gmres(S, 0.0, b, 1e-10 * np.linalg.norm(b), 30, 100, False, "dcgs2")
+    assert res.converged and res.iters == 4 and res.cycles == 1
+    assert np.allclose(res.x, b / d)
