@@ -43,9 +43,12 @@ def parse():
     ap.add_argument("--strategy", default="nobl_mid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload among the variants")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"],
                     help="precision of the headline solve (the benchmark line uses fp32: float32 "
                          "Krylov basis and sweeps, float64 outer iteration)")
+    ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"],
+                    help="Arnoldi orthogonalisation of the inner GMRES (all runs of the line)")
     ap.add_argument("--kmax", type=int, default=50,
                     help="outer step cap (a small value gives a short case for profilers)")
     ap.add_argument("--cpu-sample-its", type=int, default=60)
@@ -203,6 +206,8 @@ def run_reference(a):
 
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 float64 rate (nominal, dense)
 SWEEPS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
+# with the delayed CGS2 the first and third counters hold its two kernels
+DCGS2_NAMES = {"arnoldi_spmv": "k_dcgs_a (product + all dots)", "cgs_pass3": "k_dcgs_b (basis update)"}
 # DRAM traffic / algorithmic bytes of the sweep kernels from one ncu capture
 # of the current kernels (None once a kernel changes after its capture)
 NCU_TRAFFIC_RATIO = {}
@@ -227,7 +232,7 @@ def run_ours(a):
     # (shift selection runs sparse LU solves; the solver calls release the GIL)
     from concurrent.futures import ThreadPoolExecutor
     pool = ThreadPoolExecutor(max_workers=1)
-    batch_future = None if a.no_variants else pool.submit(W.batch_problems, 64)
+    batch_future = None if (a.no_variants or a.no_batch) else pool.submit(W.batch_problems, 64)
     stream = torch.cuda.Stream()
     jac = int(p.opts.get("jacobi", False))
     rst = p.opts.get("restart", 30)
@@ -241,6 +246,7 @@ def run_ours(a):
 
     def make(**kw):
         kw.setdefault("kmax", a.kmax)
+        kw.setdefault("ortho", a.ortho)
         return P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, stream=stream,
                               jacobi=jac, restart=rst, **kw)
 
@@ -279,13 +285,16 @@ def run_ours(a):
                 "kernel_ms_per_solve": {k: round(v[0] / max(1, solver.timed_solves), 2)
                                         for k, v in stats.items() if v[3] > 0}}, info, stats
 
+    def kname(k):
+        return DCGS2_NAMES.get(k, k) if a.ortho == "dcgs2" else k
+
     def kernel_table(stats):
         total_ms = sum(v[0] for v in stats.values())
-        return {k: {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
+        return {kname(k): {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
                     "launches": v[3],
                     "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None,
                     "TFLOPs": round(v[2] / (v[0] * 1e-3) / 1e12, 4) if v[0] > 0 else None}
-                for k, v in stats.items()}
+                for k, v in stats.items() if v[3] > 0}
 
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -316,9 +325,10 @@ def run_ours(a):
     fh = torch.from_numpy(np.asfortranarray(p.f)).pin_memory()
     gh = torch.from_numpy(np.asfortranarray(p.g)).pin_memory()
     kr = info["kr"]
-    Zh = torch.empty((kr, n), dtype=torch.float64).pin_memory()
-    Yh = torch.empty((kr, m), dtype=torch.float64).pin_memory()
-    gmh = torch.empty(kr, dtype=torch.float64).pin_memory()
+    fdt = torch.complex128 if info["is_complex"] else torch.float64
+    Zh = torch.empty((kr, n), dtype=fdt).pin_memory()
+    Yh = torch.empty((kr, m), dtype=fdt).pin_memory()
+    gmh = torch.empty(kr, dtype=fdt).pin_memory()
     e2e = []
     for k in range(a.steps):
         flush.zero_()
@@ -343,7 +353,8 @@ def run_ours(a):
                 ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2, True),
                 # one CUDA graph per solve, device-set conditional nodes (no kernel events)
                 ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 3, False),
-                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False)):
+                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False),
+                ("fp32_cgs2", dict(strategy=a.strategy, precision="fp32", ortho="cgs2"), 1, 2, True)):
             sv = make(**kw)
             tv, stv = timed(sv, w_, k_, profile=prof)
             variants[name], _, vst = summary(sv, tv, stv)
@@ -363,10 +374,10 @@ def run_ours(a):
         variants["speedup_fp64_adaptive_vs_fp64_fixed_1e-12"] = fixed / variants["fp64"]["s"]
 
         # ---- batched workload: 64 independent 2D instances in one device loop ----
-        probs = batch_future.result()
-        for prec in ("fp32", "fp64"):
+        probs = batch_future.result() if batch_future is not None else []
+        for prec, orth in ((("fp32", "cgs2"), ("fp32", "dcgs2"), ("fp64", "cgs2")) if probs else ()):
             with P.SylvesterADIBatch(probs, stream=stream, strategy=a.strategy, precision=prec, jacobi=1,
-                                     restart=30) as bt:
+                                     restart=30, ortho=orth) as bt:
                 nsolve = 0
                 bt.solve()
                 nsolve += 1
@@ -386,7 +397,7 @@ def run_ours(a):
                 tb = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in evb) / 1e3 / 2, "cuda")
                 infos = [bt.info(i) for i in range(len(probs))]
                 bs = bt.stats()
-                variants[f"batch64_{prec}"] = {
+                variants[f"batch64_{prec}_{orth}"] = {
                     "s": tb, "instances_per_s": len(probs) / tb, "status": stb,
                     "converged": sum(1 for q, i_ in zip(probs, infos) if i_["status"] == 0 and i_["rel_res_comp"] < q.tau),
                     "outer_steps_total": sum(i_["steps"] for i_ in infos),
@@ -409,13 +420,14 @@ def run_ours(a):
         "data": "synthetic",
         "config": {"workload": a.workload, "n": n, "m": m, "r": r, "restart": rst,
                    "jacobi": bool(jac), "strategy": a.strategy, "tau": p.tau, "precision": a.precision,
-                   "kmax": a.kmax, "driver": "host (per-kernel CUDA events on every 4th device iteration)",
+                   "kmax": a.kmax, "ortho": a.ortho,
+                   "driver": "host (per-kernel CUDA events on every 4th device iteration)",
                    "shifts": len(p.alpha), "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "flushed (512 MiB write) before every timed solve",
                    "outer_steps": info["steps"], "inner_its_A": info["inner_its_A"],
                    "inner_its_B": info["inner_its_B"], "rel_res_comp": info["rel_res_comp"],
                    "status": st, "device_bytes_of_solver": footprint},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach_gb, "peak": hbm, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": kname(dom), "achieved": ach_gb, "peak": hbm, "unit": "GB/s",
                      "frac": (ach_gb / hbm) if ach_gb else None, "peak_source": hbm_src,
                      "traffic": (ratio * by / la) if ratio else None,
                      "sweeps_GBps": main_sum["spmm_orth_GBps"],
@@ -425,7 +437,7 @@ def run_ours(a):
         "gpu_launches": info["launches"] * a.steps,
         "clocks": clocks,
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": (n + m) * r * 8,
-                "d2h_bytes_per_step": (n + m) * kr * 8 + kr * 8},
+                "d2h_bytes_per_step": ((n + m) * kr + kr) * (16 if info["is_complex"] else 8)},
     }
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.workload, a.strategy, a.cpu_sample_its, info)

@@ -117,7 +117,7 @@ struct Batch : BatchBase {
         max_inner = o.max_inner;
         long long total_rows = 0;
         for (const auto& p : ps) total_rows += (long long)(p.n + p.m) * p.r;
-        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk : sweep_rows_per_chunk<T, S, C>(total_rows);
+        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk : sweep_rows_per_chunk<T, S, C>(total_rows, o.ortho);
         rpc = (rpc + 31) / 32 * 32;
         // ---- layout of every instance's buffers in one arena ----
         struct Off { size_t f, g, w, t, Z, Y, gam, hist, alpha, beta, pinvA, pinvB, avalA, avalB, gpart; };
@@ -165,8 +165,8 @@ struct Batch : BatchBase {
                 pv.push_back((T*)at(off[i].pinvB)); av.push_back((C*)at(off[i].avalB));
             }
         }
-        SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, o.restart, rpc, stream));
         eng.ortho = o.ortho;
+        SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, o.restart, rpc, stream));
         SYLV_TRY(st.alloc(count));
         SYLV_CK(cudaMemset(st.p, 0, (size_t)count * sizeof(AdiState<T>)));
         // ---- per-instance descriptors and the outer-kernel work list ----
@@ -282,8 +282,9 @@ struct Batch : BatchBase {
         ip.conditional.size = 1;
         SYLV_CK(cudaGraphAddNode(&n_if, body, &n3, nullptr, 1, &ip));
         cudaGraph_t if_body = ip.conditional.phGraph_out[0];
-        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, ni, a4));
-        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, ni, a5));
+        const int rg = eng.restart_grid();
+        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, a4));
+        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, a5));
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
         BatchCtl c{};
         SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));

@@ -302,6 +302,7 @@ struct BatchCtl {
     cudaGraphConditionalHandle h_outer;    // WHILE: outer steps of Algorithm 1
     unsigned long long launch_count[K_COUNT];  // launches, counted by block 0 of each kernel
     int n_inst_open;        // batched solves: instances not finished (0 for a single solve)
+    int nitems;             // work items of the batch (grid-stride kernels)
 };
 
 __device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {

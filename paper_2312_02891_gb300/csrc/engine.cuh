@@ -42,12 +42,14 @@ inline size_t round_ld(size_t n) { return (n + 31) / 32 * 32; }
 template <typename T, typename S, typename C>
 int sweep_kernel_setup() {
     const int b = sweep_smem_bytes<S, C>();
-    if (b <= 48 * 1024) return SYLV_OK;
-    SYLV_CK(cudaFuncSetAttribute(k_arnoldi_spmv<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-    SYLV_CK(cudaFuncSetAttribute(k_cgs_pass2<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-    SYLV_CK(cudaFuncSetAttribute(k_cgs_pass3<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-    SYLV_CK(cudaFuncSetAttribute(k_dcgs_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-    SYLV_CK(cudaFuncSetAttribute(k_dcgs_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    if constexpr (sweep_smem_bytes<S, C>() > 48 * 1024) {
+        SYLV_CK(cudaFuncSetAttribute(k_arnoldi_spmv<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        SYLV_CK(cudaFuncSetAttribute(k_cgs_pass2<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        SYLV_CK(cudaFuncSetAttribute(k_cgs_pass3<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        SYLV_CK(cudaFuncSetAttribute(k_dcgs_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        SYLV_CK(cudaFuncSetAttribute(k_dcgs_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    }
+    (void)b;
     return SYLV_OK;
 }
 
@@ -57,11 +59,13 @@ int sweep_kernel_setup() {
 // costs; measured best on the 2D benchmark workload), two waves for the
 // float64 sweeps (one resident block per SM).
 template <typename T, typename S, typename C>
-int sweep_rows_per_chunk(long long total_rows) {
+int sweep_rows_per_chunk(long long total_rows, int ortho) {
+    // the wave is set by the sweep kernel with the fewest resident blocks
+    // (the delayed-CGS2 dot kernel holds twice the accumulators)
     int per_sm = 0;
+    const void* fn = ortho == 1 ? (const void*)k_dcgs_a<T, S, C> : (const void*)k_cgs_pass2<T, S, C>;
     if (sweep_kernel_setup<T, S, C>() != SYLV_OK ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_pass2<T, S, C>, SYLV_BLOCK,
-                                                      sweep_smem_bytes<S, C>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SYLV_BLOCK, sweep_smem_bytes<S, C>()) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const long long waves = SweepOcc<C>::value > 1 ? 1 : 2;
@@ -127,7 +131,7 @@ struct Engine {
         SYLV_TRY((sweep_kernel_setup<T, S, C>()));
         long long total_rows = 0;
         for (int q = 0; q < nsys; ++q) total_rows += sys_n[q];
-        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(total_rows);
+        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(total_rows, ortho);
         rpc = (rpc + 31) / 32 * 32;       // chunks hold whole 32-row basis tiles
         size_t vtot = 0, wtot = 0, ptot = 0;
         std::vector<Item> items;
@@ -180,10 +184,14 @@ struct Engine {
         SYLV_CK(cudaHostGetDevicePointer((void**)&d_hflag, h_flag, 0));
         BatchCtl c{};
         c.h_flag = d_hflag;
+        c.nitems = nitems;
         SYLV_CK(cudaMemcpy(d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         for (auto& e : ev) SYLV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         return SYLV_OK;
     }
+
+    // Blocks of the restart kernels (grid-stride over the work items).
+    int restart_grid() const { return std::max(1, std::min(nitems, 2 * num_sms())); }
 
     // One device iteration: every active system advances one Arnoldi step
     // and restarts if its cycle ended.
@@ -216,9 +224,10 @@ struct Engine {
             SYLV_TRY(mark(K_CGS3));
         }
         if (cgs_mode == 0) {
-            k_restart_update<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            const dim3 rgrid(restart_grid());
+            k_restart_update<T, S, C><<<rgrid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
             SYLV_TRY(mark(K_RUPD));
-            k_restart_residual<T, S, C><<<grid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            k_restart_residual<T, S, C><<<rgrid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
             SYLV_TRY(mark(K_RRES));
         }
         if (pe) pending[slot] = nk;
@@ -395,6 +404,7 @@ int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int nc
     BatchCtl c{};
     c.n_active = ncols;
     c.h_flag = eng.d_hflag;
+    c.nitems = eng.nitems;
     SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
     SYLV_TRY((shifted_op_setup<T, C>(op.desc, sigma, pinv.p, aval.p, s)));
     k_zero_x<T, S, C><<<eng.nitems, SYLV_BLOCK, 0, s>>>(eng.d_sd.p, eng.d_st.p, eng.d_items.p);
@@ -449,6 +459,7 @@ int cgs2_t(const void* V, int n, int k, void* w, void* h, cudaStream_t s) {
     BatchCtl c{};
     c.n_active = 1;
     c.h_flag = eng.d_hflag;
+    c.nitems = eng.nitems;
     SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
     SYLV_TRY(eng.launch_tick(1));
     SYLV_CK(cudaStreamSynchronize(s));
@@ -508,7 +519,7 @@ struct Adi : AdiBase {
         stream = a.stream;
         n = a.n; m = a.m; r = a.r; kmax = a.o.kmax; max_inner = a.o.max_inner;
         const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
-                                               : sweep_rows_per_chunk<T, S, C>((long long)(n + m) * r);
+                                               : sweep_rows_per_chunk<T, S, C>((long long)(n + m) * r, a.o.ortho);
         SYLV_TRY(f.alloc((size_t)n * r));
         SYLV_TRY(g.alloc((size_t)m * r));
         SYLV_TRY(w.alloc((size_t)n * r));
@@ -545,6 +556,7 @@ struct Adi : AdiBase {
         for (int l = 0; l < r; ++l) { sn.push_back(n); so.push_back(0); pv.push_back(pinvA.p); av.push_back(avalA.p); }
         for (int l = 0; l < r; ++l) { sn.push_back(m); so.push_back(1); pv.push_back(pinvB.p); av.push_back(avalB.p); }
         std::vector<OpDesc> ops{a.A->desc, a.Bt->desc};
+        eng.ortho = a.o.ortho;
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, a.o.restart, rpc, stream));
         const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
         SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
@@ -566,7 +578,6 @@ struct Adi : AdiBase {
         d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
         d.s = st.p; d.h_done = d_hdone;
         graph_on = a.o.driver == 0 ? 1 : 0;
-        eng.ortho = a.o.ortho;
         return SYLV_OK;
     }
 
@@ -675,8 +686,9 @@ struct Adi : AdiBase {
             SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_cgs_pass3<T, S, C>, ni, SYLV_BLOCK, a3, sm));
         }
         SYLV_TRY(add_cond(&n_if, loop_body, &n3, h_restart, cudaGraphCondTypeIf, &if_body));
-        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, ni, SYLV_BLOCK, a4));
-        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, ni, SYLV_BLOCK, a5));
+        const int rg = eng.restart_grid();
+        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, SYLV_BLOCK, a4));
+        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, SYLV_BLOCK, a5));
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
         // the kernels read the handles and the decision parameters from the control block
         BatchCtl c{};

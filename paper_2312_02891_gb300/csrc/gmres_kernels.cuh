@@ -167,11 +167,12 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// Runs body(i, sv, wv) for every row i < r1 of the warp's tiles in [t0, t1),
-// with sv[32 l] = V_l(i) (l < nv) and wv = w(i) read from the stage.
-template <int NV, typename S, typename C, typename Body>
-__device__ __forceinline__ void stream_tiles(const S* __restrict__ V, size_t tstride, const C* __restrict__ w,
-                                             int t0, int t1, int r1, int nv, Body body) {
+// The stage pipeline: tile_body(t, sv, sw) runs, by the whole warp, for
+// every tile t of the warp in [t0, t1), with sv[32 l + r] = V_l(32 t + r)
+// (l < nv) and sw[r] = w(32 t + r) in shared memory.
+template <int NV, typename S, typename C, typename TileBody>
+__device__ __forceinline__ void stream_tile_stages(const S* __restrict__ V, size_t tstride, const C* __restrict__ w,
+                                                   int t0, int t1, int nv, TileBody tile_body) {
     extern __shared__ __align__(16) unsigned char sweep_dsm[];
     constexpr int NVS = NV < SYLV_MAXV ? NV : SYLV_MAXV;               // vectors a stage must hold
     constexpr int VB = NVS * 32 * (int)sizeof(S);                       // basis bytes of a tile
@@ -204,10 +205,22 @@ __device__ __forceinline__ void stream_tiles(const S* __restrict__ V, size_t tst
         cp_async_wait<P>();
         __syncwarp();
         const unsigned char* st = wsm + (q % NST) * TB;
-        const int i = (t0 + warp + q * SYLV_NWARP) * 32 + lane;
-        if (i < r1) body(i, reinterpret_cast<const S*>(st) + lane, reinterpret_cast<const C*>(st + VB)[lane]);
+        tile_body(t0 + warp + q * SYLV_NWARP, reinterpret_cast<const S*>(st), reinterpret_cast<const C*>(st + VB));
         __syncwarp();
     }
+}
+
+// Runs body(i, sv, wv) for every row i < r1 of the warp's tiles in [t0, t1),
+// lane = row of the tile, with sv[32 l] = V_l(i) (l < nv) and wv = w(i) read
+// from the stage.
+template <int NV, typename S, typename C, typename Body>
+__device__ __forceinline__ void stream_tiles(const S* __restrict__ V, size_t tstride, const C* __restrict__ w,
+                                             int t0, int t1, int r1, int nv, Body body) {
+    const int lane = threadIdx.x & 31;
+    stream_tile_stages<NV, S, C>(V, tstride, w, t0, t1, nv, [&](int t, const S* sv, const C* sw) {
+        const int i = t * 32 + lane;
+        if (i < r1) body(i, sv + lane, sw[lane]);
+    });
 }
 
 // Row i of w = (Op + sigma I) P^{-1} (sj * V_j): the pre-scaled stencil
@@ -273,7 +286,10 @@ __device__ __forceinline__ void spmv_rows(const SysDesc<T, S, C>& sd, const OpDe
         // warp-tile order of the staged sweep (each warp then stages only
         // rows it wrote itself), then the dot products from shared memory
         if (mode == 0) {
+            // two row tiles per warp in flight: the stencil gathers of
+            // independent rows overlap (four spill at 80 registers)
             const int lane = threadIdx.x & 31;
+#pragma unroll 2
             for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
                 const int i = t * 32 + lane;
                 if (i < r1) w[i] = spmv_row<LAY>(sd, op, st, vj, sj, i);
@@ -421,10 +437,9 @@ k_cgs_pass2(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__
 // sequential parts.
 template <typename T>
 __device__ int hess_column_finish(int restart, double* hist, int hist_cap, SysState<T>* st, int c, const T* s_col,
-                                  double hn) {
+                                  double hn, T* s_R /* shared, SYLV_MR * SYLV_MAXV */) {
     __shared__ T s_sn[SYLV_MR];
     __shared__ double s_cs[SYLV_MR];
-    __shared__ T s_R[SYLV_MR * SYLV_MAXV];
     __shared__ T s_g[SYLV_MAXV];
     __shared__ int s_end;
     for (int i = threadIdx.x; i <= c; i += blockDim.x) {
@@ -505,12 +520,13 @@ __device__ int hess_column_finish(int restart, double* hist, int hist_cap, SysSt
 template <typename T>
 __device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState<T>* st, double nrm2) {
     __shared__ T s_col[SYLV_MAXV];
+    __shared__ T s_R[SYLV_MR * SYLV_MAXV];
     const int j = st->j;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = st->h1[i] + st->h2[i];
     __syncthreads();
     const double hn = sqrt(nrm2);
     if (threadIdx.x == 0) st->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    const int end = hess_column_finish<T>(restart, hist, hist_cap, st, j, s_col, hn);
+    const int end = hess_column_finish<T>(restart, hist, hist_cap, st, j, s_col, hn, s_R);
     if (end == 0 && threadIdx.x == 0) st->j = j + 1;
 }
 
@@ -690,6 +706,7 @@ __device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const Op
     if constexpr (Staged<S, C>::value) {
         if (product) {
             const int lane = threadIdx.x & 31;
+#pragma unroll 2
             for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
                 const int i = t * 32 + lane;
                 if (i < r1) w[i] = spmv_row<1>(sd, op, st, uj, sj, i);
@@ -767,8 +784,12 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     // ---- the step's sequential part: one block per system ----
     __shared__ T tot[PSTRIDE];
     __shared__ T s_s[SYLV_MAXV], s_z[SYLV_MAXV], s_col[SYLV_MAXV];
+    __shared__ T s_H[SYLV_MR * SYLV_MAXV];      // Hessenberg columns 0..j-1 as formed
+    __shared__ T s_R[SYLV_MR * SYLV_MAXV];      // rotated columns (Givens scratch)
     __shared__ double s_beta;
     __shared__ T s_vy;
+    // the columns formed so far, in parallel (read below by the first pass of column j)
+    for (int q = threadIdx.x; q < (j > 0 ? (j - 1) * SYLV_MAXV : 0); q += blockDim.x) s_H[q] = st->Hr[q];
     reduce_chunks(sd.part, sd.nchunks, PSTRIDE, 2 * j + 2, tot);
     for (int l = threadIdx.x; l < j; l += blockDim.x) {
         s_s[l] = (st->scale[l] * sj) * tot[l];
@@ -786,13 +807,14 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     const double beta = s_beta;
     int end = 0;
     if (j >= 1) {
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            s_col[i] = st->h1[i] + s_s[i];
-            st->Hr[(j - 1) * SYLV_MAXV + i] = s_col[i];
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            const T v = i < j ? st->h1[i] + s_s[i] : make_scalar<T>(beta, 0.0);
+            if (i < j) s_col[i] = v;
+            s_H[(j - 1) * SYLV_MAXV + i] = v;
+            st->Hr[(j - 1) * SYLV_MAXV + i] = v;
         }
-        if (threadIdx.x == 0) st->Hr[(j - 1) * SYLV_MAXV + j] = make_scalar<T>(beta, 0.0);
         __syncthreads();
-        end = hess_column_finish<T>(sd.restart, sd.hist, sd.hist_cap, st, j - 1, s_col, beta);
+        end = hess_column_finish<T>(sd.restart, sd.hist, sd.hist_cap, st, j - 1, s_col, beta, s_R);
     } else if (!(beta > 0.0) || !isfinite(beta)) {
         if (threadIdx.x == 0) {
             if (!isfinite(beta)) st->status = ST_NONFINITE;
@@ -815,7 +837,7 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     const double ib = 1.0 / beta;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         T hs = zero<T>();                        // (H s)_i over the first j columns
-        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += st->Hr[c * SYLV_MAXV + i] * s_s[c];
+        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += s_H[c * SYLV_MAXV + i] * s_s[c];
         const T zi = i < j ? s_z[i] : s_vy;
         st->h1[i] = ib * (zi - hs);
     }
@@ -909,12 +931,12 @@ k_dcgs_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // Restart, part 1: x += P^{-1} sum_l y_l V_l  (y already carries the scales).
 // The combination is formed in the sweep precision C, the update in float64.
 // ---------------------------------------------------------------------------
+// The restart kernels run every device iteration but have work only when a
+// cycle ends: a grid of a few blocks per SM strides over the work items, so
+// an idle launch is cheap.
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
-k_restart_update(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
-                 const Item* __restrict__ items, BatchCtl* ctl) {
-    count_launch(ctl, K_RUPD);
-    const Item it = items[blockIdx.x];
+__device__ __forceinline__ void restart_update_item(const SysDesc<T, S, C>* __restrict__ sysd,
+                                                    SysState<T>* __restrict__ sts, const Item it, BatchCtl* ctl) {
     SysState<T>* st = sts + it.sys;
     if (st->phase != PH_UPDATE) return;
     const SysDesc<T, S, C> sd = sysd[it.sys];
@@ -940,18 +962,27 @@ k_restart_update(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restr
 #undef SYLV_RUPD_CALL
 }
 
+template <typename T, typename S, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK)
+k_restart_update(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
+                 const Item* __restrict__ items, BatchCtl* ctl) {
+    count_launch(ctl, K_RUPD);
+    const int ni = ctl->nitems;
+    for (int q = blockIdx.x; q < ni; q += gridDim.x) {
+        restart_update_item<T, S, C>(sysd, sts, items[q], ctl);
+        __syncthreads();          // shared coefficients are rewritten by the next item
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Restart, part 2: r = b - (Op + sigma I) x (float64), V_0 = r, ||r||, then
 // the decision: converged / iteration cap / non-finite -> done, else a new
 // cycle with v_0 = r / ||r||.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__device__ __forceinline__ void restart_residual_body(const SysDesc<T, S, C>* __restrict__ sysd,
+__device__ __forceinline__ void restart_residual_item(const SysDesc<T, S, C>* __restrict__ sysd,
                                                       SysState<T>* __restrict__ sts,
-                                                      const OpDesc* __restrict__ ops,
-                                                      const Item* __restrict__ items, BatchCtl* ctl) {
-    count_launch(ctl, K_RRES);
-    const Item it = items[blockIdx.x];
+                                                      const OpDesc* __restrict__ ops, const Item it, BatchCtl* ctl) {
     SysState<T>* st = sts + it.sys;
     const int ph = st->phase;
     if (ph != PH_UPDATE && ph != PH_RESID) return;
@@ -1008,7 +1039,12 @@ template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK)
 k_restart_residual(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
                    const OpDesc* __restrict__ ops, const Item* __restrict__ items, BatchCtl* ctl) {
-    restart_residual_body<T, S, C>(sysd, sts, ops, items, ctl);
+    count_launch(ctl, K_RRES);
+    const int ni = ctl->nitems;
+    for (int q = blockIdx.x; q < ni; q += gridDim.x) {
+        restart_residual_item<T, S, C>(sysd, sts, ops, items[q], ctl);
+        __syncthreads();          // shared reduction buffers are reused by the next item
+    }
     if (ctl->graph) graph_tail<T>(ctl, sts, K_RRES);
 }
 
