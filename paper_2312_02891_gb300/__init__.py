@@ -71,7 +71,7 @@ class SylvOpts(C.Structure):
                 ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
                 ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32),
-                ("ortho", C.c_int32)]
+                ("ortho", C.c_int32), ("restart_every", C.c_int32)]
 
 
 class SylvProblem(C.Structure):

@@ -66,6 +66,10 @@ static int resolve_opts(const sylv_opts* opts, double tol, sylv_opts* o) {
         set_error("invalid options (kmax, max_inner, strategy, xi or dmax)");
         return SYLV_ERR_INVALID;
     }
+    if (o->restart_every < 0) {
+        set_error("restart_every %d < 0", o->restart_every);
+        return SYLV_ERR_INVALID;
+    }
     if (o->ortho != SYLV_ORTHO_CGS2 && o->ortho != SYLV_ORTHO_DCGS2) {
         set_error("unknown orthogonalisation %d", o->ortho);
         return SYLV_ERR_INVALID;
@@ -98,6 +102,7 @@ int sylv_opts_default(sylv_opts* o) {
     o->rows_per_chunk = 0;
     o->driver = 1;
     o->ortho = SYLV_ORTHO_CGS2;
+    o->restart_every = 4;
     return SYLV_OK;
 }
 

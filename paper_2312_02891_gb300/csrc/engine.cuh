@@ -103,6 +103,7 @@ struct Engine {
     int pending[4] = {0, 0, 0, 0};
     int pkid[4][5] = {};                // kernel id of each timed interval
     int ortho = 0;                      // 0: CGS2 (three sweeps), 1: delayed CGS2 (two sweeps)
+    int restart_every = 1;              // host driver: restart kernels every k-th device iteration
     double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
     long long samples[K_COUNT] = {};    // sampled launches
     long long launches[K_COUNT] = {};   // all launches
@@ -196,7 +197,7 @@ struct Engine {
     // One device iteration: every active system advances one Arnoldi step
     // and restarts if its cycle ended.
     // With profiling on, every prof_every-th tick is bracketed by events.
-    int launch_tick(int cgs_mode = 0, int slot = 0) {
+    int launch_tick(int cgs_mode = 0, int slot = 0, bool with_restart = true) {
         const dim3 grid(nitems), block(SYLV_BLOCK);
         cudaEvent_t* pe = (profile && (tick_no++ % prof_every) == 0) ? pev[slot] : nullptr;
         if (pe) SYLV_CK(cudaEventRecord(pe[0], stream));
@@ -223,7 +224,7 @@ struct Engine {
             k_cgs_pass3<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p, cgs_mode);
             SYLV_TRY(mark(K_CGS3));
         }
-        if (cgs_mode == 0) {
+        if (cgs_mode == 0 && with_restart) {
             const dim3 rgrid(restart_grid());
             k_restart_update<T, S, C><<<rgrid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
             SYLV_TRY(mark(K_RUPD));
@@ -271,7 +272,10 @@ struct Engine {
 
     // Launch ticks until every system is done (the device clears *h_flag),
     // keeping at most four ticks in flight.  The caller sets *h_flag = 1
-    // before the work that activates the systems.
+    // before the work that activates the systems.  The restart kernels run
+    // in the first tick and then every restart_every-th one: a system whose
+    // cycle ended waits (its sweeps skip it) until the next restart tick, and
+    // its arithmetic does not change.
     int run(long long max_ticks) {
         const int D = 4;
         long long t = 0;
@@ -282,7 +286,7 @@ struct Engine {
             }
             const int slot = (int)(t % D);
             if (pending[slot]) SYLV_TRY(harvest(slot));
-            SYLV_TRY(launch_tick(0, slot));
+            SYLV_TRY(launch_tick(0, slot, restart_every <= 1 || t % restart_every == 0));
             SYLV_CK(cudaEventRecord(ev[slot], stream));
             ++t;
             if (t >= D) SYLV_CK(cudaEventSynchronize(ev[t % D]));
@@ -578,6 +582,7 @@ struct Adi : AdiBase {
         d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
         d.s = st.p; d.h_done = d_hdone;
         graph_on = a.o.driver == 0 ? 1 : 0;
+        eng.restart_every = a.o.restart_every;
         return SYLV_OK;
     }
 

@@ -239,3 +239,20 @@ def test_dcgs2_graph_and_host_agree_bitwise(precision):
         out.append((info["steps"], Z, Y, gam))
     assert out[0][0] == out[1][0]
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][3], out[1][3])
+
+
+@pytest.mark.parametrize("ortho", ["cgs2", "dcgs2"])
+def test_restart_stride_keeps_results_bitwise(ortho):
+    """Host driver with the restart kernels launched every third device
+    iteration: systems wait for their restart, their arithmetic is the same,
+    so the factors agree bit for bit with the every-iteration launch."""
+    p = problem("tiny2d")
+    out = []
+    for every in (1, 3):
+        st, info, hist, Z, Y, gam = run_gpu(p, strategy="nobl_mid", jacobi=1, precision="fp32", driver=1,
+                                            ortho=ortho, restart_every=every)
+        assert st == 0
+        out.append((info["steps"], info["inner_its_A"], Z, gam, info["ticks"]))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+    assert out[1][4] >= out[0][4]          # waiting costs device iterations, never saves them
