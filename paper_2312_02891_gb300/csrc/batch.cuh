@@ -115,9 +115,10 @@ struct Batch : BatchBase {
         count = (int)ps.size();
         kmax = o.kmax;
         max_inner = o.max_inner;
-        long long total_rows = 0;
-        for (const auto& p : ps) total_rows += (long long)(p.n + p.m) * p.r;
-        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk : sweep_rows_per_chunk<T, S, C>(total_rows, o.ortho);
+        std::vector<long long> rows;
+        for (const auto& p : ps)
+            for (int l = 0; l < p.r; ++l) { rows.push_back(p.n); rows.push_back(p.m); }
+        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk : sweep_rows_per_chunk<T, S, C>(rows, o.ortho);
         rpc = (rpc + 31) / 32 * 32;
         // ---- layout of every instance's buffers in one arena ----
         struct Off { size_t f, g, w, t, Z, Y, gam, hist, alpha, beta, pinvA, pinvB, avalA, avalB, gpart; };
@@ -259,6 +260,8 @@ struct Batch : BatchBase {
         void* ao[] = {&dsp, &bip, &ctp};
         void* a1[] = {&sdp, &stp, &opp, &itp, &ctp, &mode0};
         void* a2[] = {&sdp, &stp, &itp, &ctp};
+        int nsysb = eng.nsys;
+        void* ab[] = {&sdp, &stp, &itp, &ctp, &nsysb};
         void* a3[] = {&sdp, &stp, &itp, &ctp, &mode0};
         void* a4[] = {&sdp, &stp, &itp, &ctp};
         void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
@@ -268,8 +271,8 @@ struct Batch : BatchBase {
         SYLV_TRY(add_kernel(&n_s, body, &n_o, (void*)k_batch_step<T, S, C>, nbitems, ao));
         const int sm = sweep_smem_bytes<S, C>();
         if (eng.ortho == 1) {
-            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, sm));
-            SYLV_TRY(add_kernel(&n3, body, &n1, (void*)k_dcgs_b<T, S, C>, ni, a2, sm));
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, dcgs_a_smem_bytes<T, S, C>()));
+            SYLV_TRY(add_kernel(&n3, body, &n1, (void*)k_dcgs_b<T, S, C>, ni + nsysb, ab, dcgs_b_smem_bytes<T, S, C>()));
         } else {
             SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_arnoldi_spmv<T, S, C>, ni, a1, sm));
             SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, a2, sm));

@@ -276,6 +276,7 @@ struct SysState {
     double sjb;
     int jb;
     int upd;
+    int gpend;              // delayed CGS2: Hessenberg column gpend - 1 awaits its Givens update (0: none)
 };
 
 // Work item of a launch: (system, chunk).

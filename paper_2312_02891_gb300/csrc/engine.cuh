@@ -46,9 +46,13 @@ int sweep_kernel_setup() {
         SYLV_CK(cudaFuncSetAttribute(k_arnoldi_spmv<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         SYLV_CK(cudaFuncSetAttribute(k_cgs_pass2<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         SYLV_CK(cudaFuncSetAttribute(k_cgs_pass3<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        SYLV_CK(cudaFuncSetAttribute(k_dcgs_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        SYLV_CK(cudaFuncSetAttribute(k_dcgs_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
     }
+    if constexpr (dcgs_b_smem_bytes<T, S, C>() > 48 * 1024)
+        SYLV_CK(cudaFuncSetAttribute(k_dcgs_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dcgs_b_smem_bytes<T, S, C>()));
+    if constexpr (dcgs_a_smem_bytes<T, S, C>() > 48 * 1024)
+        SYLV_CK(cudaFuncSetAttribute(k_dcgs_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dcgs_a_smem_bytes<T, S, C>()));
     (void)b;
     return SYLV_OK;
 }
@@ -57,22 +61,36 @@ int sweep_kernel_setup() {
 // 256 rows: one wave of resident blocks over all rows of the batch for the
 // 32-bit sweeps (several resident blocks per SM hide each other's fixed
 // costs; measured best on the 2D benchmark workload), two waves for the
-// float64 sweeps (one resident block per SM).
+// float64 sweeps (one resident block per SM).  sys_rows holds the rows of
+// every system: each system rounds its chunk count up, so the chunk is
+// widened (by at most a quarter) until all chunks fit the wave - a block
+// left over for a second wave delays its system's reduction by a whole
+// block's work.
 template <typename T, typename S, typename C>
-int sweep_rows_per_chunk(long long total_rows, int ortho) {
+int sweep_rows_per_chunk(const std::vector<long long>& sys_rows, int ortho) {
+    long long total_rows = 0;
+    for (long long q : sys_rows) total_rows += q;
     // the wave is set by the sweep kernel with the fewest resident blocks
     // (the delayed-CGS2 dot kernel holds twice the accumulators)
     int per_sm = 0;
     const void* fn = ortho == 1 ? (const void*)k_dcgs_a<T, S, C> : (const void*)k_cgs_pass2<T, S, C>;
+    const int smem = ortho == 1 ? dcgs_a_smem_bytes<T, S, C>() : sweep_smem_bytes<S, C>();
     if (sweep_kernel_setup<T, S, C>() != SYLV_OK ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SYLV_BLOCK, sweep_smem_bytes<S, C>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SYLV_BLOCK, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const long long waves = SweepOcc<C>::value > 1 ? 1 : 2;
     const long long items = waves * num_sms() * per_sm;
     long long rpc = (total_rows + items - 1) / items;
-    rpc = (rpc + 31) / 32 * 32;
-    return (int)std::max<long long>(256, std::min<long long>(rpc, 1 << 16));
+    rpc = std::max<long long>(256, std::min<long long>((rpc + 31) / 32 * 32, 1 << 16));
+    auto chunks = [&](long long c) {
+        long long k = 0;
+        for (long long q : sys_rows) k += (q + c - 1) / c;
+        return k;
+    };
+    long long fit = rpc;
+    while (chunks(fit) > items && fit + 32 <= std::min<long long>(rpc + rpc / 4, 1 << 16)) fit += 32;
+    return (int)(chunks(fit) <= items ? fit : rpc);
 }
 
 // Elements of one system's tile-major basis: whole 32-row tiles.
@@ -130,9 +148,7 @@ struct Engine {
         restart = restart_;
         nsys = (int)sys_n.size();
         SYLV_TRY((sweep_kernel_setup<T, S, C>()));
-        long long total_rows = 0;
-        for (int q = 0; q < nsys; ++q) total_rows += sys_n[q];
-        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(total_rows, ortho);
+        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(std::vector<long long>(sys_n.begin(), sys_n.end()), ortho);
         rpc = (rpc + 31) / 32 * 32;       // chunks hold whole 32-row basis tiles
         size_t vtot = 0, wtot = 0, ptot = 0;
         std::vector<Item> items;
@@ -212,9 +228,11 @@ struct Engine {
             return SYLV_OK;
         };
         if (ortho == 1 && cgs_mode == 0) {
-            k_dcgs_a<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            k_dcgs_a<T, S, C><<<grid, block, dcgs_a_smem_bytes<T, S, C>(), stream>>>(d_sd.p, d_st.p, d_ops.p,
+                                                                                    d_items.p, d_ctl.p);
             SYLV_TRY(mark(K_SPMV));
-            k_dcgs_b<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            k_dcgs_b<T, S, C><<<nitems + nsys, block, dcgs_b_smem_bytes<T, S, C>(), stream>>>(d_sd.p, d_st.p,
+                                                                                        d_items.p, d_ctl.p, nsys);
             SYLV_TRY(mark(K_CGS3));
         } else {
             k_arnoldi_spmv<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p, cgs_mode);
@@ -522,8 +540,10 @@ struct Adi : AdiBase {
     int init(const AdiArgs& a) {
         stream = a.stream;
         n = a.n; m = a.m; r = a.r; kmax = a.o.kmax; max_inner = a.o.max_inner;
+        std::vector<long long> rows;
+        for (int l = 0; l < r; ++l) { rows.push_back(n); rows.push_back(m); }
         const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
-                                               : sweep_rows_per_chunk<T, S, C>((long long)(n + m) * r, a.o.ortho);
+                                               : sweep_rows_per_chunk<T, S, C>(rows, a.o.ortho);
         SYLV_TRY(f.alloc((size_t)n * r));
         SYLV_TRY(g.alloc((size_t)m * r));
         SYLV_TRY(w.alloc((size_t)n * r));
@@ -678,13 +698,17 @@ struct Adi : AdiBase {
         auto* ctp = eng.d_ctl.p;
         void* a1[] = {&sdp, &stp, &opp, &itp, &ctp, &mode0};
         void* a2[] = {&sdp, &stp, &itp, &ctp};
+        int nsysb = eng.nsys;
+        void* ab[] = {&sdp, &stp, &itp, &ctp, &nsysb};
         void* a3[] = {&sdp, &stp, &itp, &ctp, &mode0};
         void* a4[] = {&sdp, &stp, &itp, &ctp};
         void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
         const int sm = sweep_smem_bytes<S, C>();
         if (eng.ortho == 1) {
-            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5, sm));
-            SYLV_TRY(add_kernel(&n3, loop_body, &n1, (void*)k_dcgs_b<T, S, C>, ni, SYLV_BLOCK, a2, sm));
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5,
+                                dcgs_a_smem_bytes<T, S, C>()));
+            SYLV_TRY(add_kernel(&n3, loop_body, &n1, (void*)k_dcgs_b<T, S, C>, ni + nsysb, SYLV_BLOCK, ab,
+                                dcgs_b_smem_bytes<T, S, C>()));
         } else {
             SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_arnoldi_spmv<T, S, C>, ni, SYLV_BLOCK, a1, sm));
             SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_cgs_pass2<T, S, C>, ni, SYLV_BLOCK, a2, sm));

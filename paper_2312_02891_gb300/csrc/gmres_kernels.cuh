@@ -61,17 +61,42 @@ __device__ __forceinline__ bool last_block(unsigned* counter, int nchunks) {
     return am_last != 0;
 }
 
-// tot[l] = sum over chunks c of part[c * stride + l], l < cnt; fixed order.
+// tot[l] = sum over chunks c of part[c * stride + l], l < cnt, in a fixed
+// order.  Thread t takes sum l = t mod W and the chunks c = g, g + G, ...
+// of group g = t / W (W = 32 or 64 sums per pass, G = blockDim / W groups),
+// eight loads in flight at a time; the G group sums are then added in group
+// order.  A warp reads 32 consecutive partial sums of one chunk (coalesced),
+// and the float64 adds are spread over all lanes instead of repeated per
+// warp and sum.
 template <typename T>
 __device__ __forceinline__ void reduce_chunks(const T* part, int nchunks, int stride, int cnt, T* tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int l = warp; l < cnt; l += SYLV_NWARP) {
-        T s = zero<T>();
-        for (int c = lane; c < nchunks; c += 32) s += ldcg(part + (size_t)c * stride + l);
-        s = warp_sum(s);
-        if (lane == 0) tot[l] = s;
+    __shared__ T rsum[SYLV_BLOCK];
+    const int W = cnt > 32 ? 64 : 32;
+    const int G = SYLV_BLOCK / W;
+    for (int l0 = 0; l0 < cnt; l0 += W) {
+        const int l = l0 + (int)threadIdx.x % W, g = (int)threadIdx.x / W;
+        T sum = zero<T>();
+        if (l < cnt) {
+            for (int c0 = g; c0 < nchunks; c0 += 8 * G) {
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = c0 + u * G;
+                    v[u] = c < nchunks ? ldcg(part + (size_t)c * stride + l) : zero<T>();
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sum += v[u];
+            }
+        }
+        rsum[threadIdx.x] = sum;
+        __syncthreads();
+        if ((int)threadIdx.x < W && l0 + (int)threadIdx.x < cnt) {
+            T t = rsum[threadIdx.x];
+            for (int q = 1; q < G; ++q) t += rsum[q * W + threadIdx.x];
+            tot[l0 + threadIdx.x] = t;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ double absv(double a) { return fabs(a); }
@@ -119,25 +144,31 @@ __device__ void mark_done(SysState<T>* st, BatchCtl* ctl) {
 typedef double RedBufD[SYLV_NWARP][PSTRIDE];
 
 // Per-thread accumulators (type A, NV slots) -> block sums in type T written to
-// out[0..cnt); red is a shared buffer of SYLV_NWARP x PSTRIDE T.  The warp
-// stage adds in A (float32 for the mixed path: float64 adds run at 1/58 of
-// the float32 rate on this GPU); warps and chunks are combined in T.
+// out[0..cnt); red is a shared buffer of SYLV_NWARP x PSTRIDE T (used as A).
+// The warps of the block are combined in A (float32 for the mixed path) and
+// each sum is converted to T once: on this GPU every float64 instruction,
+// conversions included, occupies the small float64 pipe for a whole warp
+// even with one active lane, so a conversion per warp and sum (lane 0 of
+// each warp) had cost more than the sweep's own arithmetic.  Chunks are
+// combined in T.
 template <typename T, typename A, int NV>
 __device__ __forceinline__ void block_reduce_to(A (&acc)[NV], int cnt, T* out, T (*red)[PSTRIDE]) {
+    static_assert(sizeof(A) <= sizeof(T), "the reduction buffer holds T");
+    A (*ra)[PSTRIDE] = reinterpret_cast<A (*)[PSTRIDE]>(red);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < NV; ++l) {
         if (l < cnt) {
             const A v = warp_sum(acc[l]);
-            if (lane == 0) red[warp][l] = cvt<T>(v);
+            if (lane == 0) ra[warp][l] = v;
         }
     }
     __syncthreads();
     for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
-        T s = zero<T>();
+        A s = ra[0][l];
 #pragma unroll
-        for (int w = 0; w < SYLV_NWARP; ++w) s += red[w][l];
-        out[l] = s;
+        for (int w = 1; w < SYLV_NWARP; ++w) s += ra[w][l];
+        out[l] = cvt<T>(s);
     }
 }
 
@@ -678,6 +709,48 @@ k_cgs_pass3(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__
 // completes the last column).
 // ---------------------------------------------------------------------------
 
+
+// w = (Op + sigma I) P^{-1} (sj u) over the warp's row tiles of [r0, r1)
+// (tiles t0 + warp, t0 + warp + NWARP, ...) for a stencil-stored operator
+// (pre-scaled diagonals aval, tile-major u) with ndiag <= ND diagonals.  U
+// tiles at a time: every load of the group (U x ndiag diagonal values and
+// neighbour entries) is issued before the first multiply-add, so a warp keeps
+// U x ndiag x 256 bytes in flight instead of waiting once per row tile.
+template <int U, int ND, typename T, typename S, typename C>
+__device__ __forceinline__ void product_tiles(const SysDesc<T, S, C>& sd, const OpDesc& op,
+                                              const S* __restrict__ uj, typename RealOf<C>::type sj,
+                                              int r0, int r1) {
+    typedef BasisIx<1> BI;
+    const C* __restrict__ av = sd.aval;
+    C* __restrict__ w = sd.w;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tend = (r1 + 31) >> 5;
+    for (int tb = (r0 >> 5) + warp; tb < tend; tb += U * SYLV_NWARP) {
+        C a[U][ND];
+        S x[U][ND];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int i = (tb + q * SYLV_NWARP) * 32 + lane;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const int k = i + op.offs[d];
+                const bool ok = d < op.ndiag && i < r1 && k >= 0 && k < op.n;
+                a[q][d] = ok ? av[(size_t)d * op.n + i] : zero<C>();
+                x[q][d] = ok ? uj[BI::row(sd, k)] : cvt<S>(zero<C>());
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int i = (tb + q * SYLV_NWARP) * 32 + lane;
+            C y = zero<C>();
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                if (d < op.ndiag) y += a[q][d] * cvt<C>(x[q][d]);
+            if (i < r1) w[i] = sj * y;
+        }
+    }
+}
+
 // Rows [r0, r1) of sweep a with NV >= j accumulators per kind.
 template <int NV, typename T, typename S, typename C>
 __device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const OpDesc& op, const SysState<T>* st,
@@ -705,11 +778,19 @@ __device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const Op
     };
     if constexpr (Staged<S, C>::value) {
         if (product) {
-            const int lane = threadIdx.x & 31;
+            if (sd.aval && op.ndiag <= 5) {
+                product_tiles<4, 5>(sd, op, uj, sj, r0, r1);      // 2D five-point stencils
+            } else if (sd.aval && op.ndiag <= 7) {
+                product_tiles<4, 7>(sd, op, uj, sj, r0, r1);      // 3D seven-point stencils
+            } else if (sd.aval) {
+                product_tiles<2, SYLV_MAXDIAG>(sd, op, uj, sj, r0, r1);
+            } else {
+                const int lane = threadIdx.x & 31;
 #pragma unroll 2
-            for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
-                const int i = t * 32 + lane;
-                if (i < r1) w[i] = spmv_row<1>(sd, op, st, uj, sj, i);
+                for (int t = (r0 >> 5) + (int)(threadIdx.x >> 5); t < ((r1 + 31) >> 5); t += SYLV_NWARP) {
+                    const int i = t * 32 + lane;
+                    if (i < r1) w[i] = spmv_row<1>(sd, op, st, uj, sj, i);
+                }
             }
             __syncwarp();
         }
@@ -729,8 +810,10 @@ __device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const Op
             body(cvt<C>(vr[BI::vec(sd, j)]), wv, [&](int l) { return vr[BI::vec(sd, l)]; });
         }
     }
-    // compact the used sums: s (j), z (j), alpha, gamma at 0..2j+1
+    // compact the used sums: s (j), z (j), alpha, gamma at 0..2j+1; warps
+    // are combined in C and each sum is converted to T once
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    C (*rc)[PSTRIDE] = reinterpret_cast<C (*)[PSTRIDE]>(red);
 #pragma unroll
     for (int q = 0; q < 2 * NV + 2; ++q) {
         const int l = q < NV ? q : (q < 2 * NV ? q - NV : q - 2 * NV);
@@ -738,16 +821,246 @@ __device__ __forceinline__ void dcgs_a_rows(const SysDesc<T, S, C>& sd, const Op
         const bool used = q < 2 * NV ? (l < j) : true;
         if (used) {
             const C v = warp_sum(acc[q]);
-            if (lane == 0) red[warp][dst] = cvt<T>(v);
+            if (lane == 0) rc[warp][dst] = v;
         }
     }
     __syncthreads();
     for (int l = threadIdx.x; l < 2 * j + 2; l += blockDim.x) {
-        T sum = zero<T>();
+        C sum = rc[0][l];
 #pragma unroll
-        for (int q = 0; q < SYLV_NWARP; ++q) sum += red[q][l];
-        out[l] = sum;
+        for (int q = 1; q < SYLV_NWARP; ++q) sum += rc[q][l];
+        out[l] = cvt<T>(sum);
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// The sequential part of a delayed-CGS2 step is split in two.  What the next
+// sweep needs - beta, the coefficients of sweep b, the first pass of column
+// j - is formed by the last block of each system in k_dcgs_a (dcgs_step_tail);
+// the Givens update of the completed column, the stop test and, at the end
+// of a cycle, the least-squares solution run in one extra block per system
+// of k_dcgs_b (dcgs_givens), beside that kernel's sweep.  On this GPU a
+// float64 instruction costs a whole warp slot of a small pipe even with one
+// active lane, so these scalar recurrences take microseconds; outside the
+// critical path they overlap the sweep.  A cycle that the Givens update ends
+// has its sweep b done for nothing (its vectors are not used).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+
+// Byte ranges [lo, hi) (multiples of 8) of *st copied to the same offsets of *ss.
+template <typename T>
+__device__ __forceinline__ void state_copy_async(const SysState<T>* st, SysState<T>* ss, size_t lo, size_t hi) {
+    const char* g = reinterpret_cast<const char*>(st);
+    char* d = reinterpret_cast<char*>(ss);
+    for (size_t q = lo / 8 + threadIdx.x; q < hi / 8; q += blockDim.x) cp_async8(d + 8 * q, g + 8 * q);
+}
+
+// Dynamic shared memory of k_dcgs_a: the sweep stages, then (in the tail) the
+// copy of the system state.
+template <typename T, typename S, typename C> constexpr int dcgs_a_smem_bytes() {
+    return sweep_smem_bytes<S, C>() > (int)sizeof(SysState<T>) ? sweep_smem_bytes<S, C>() : (int)sizeof(SysState<T>);
+}
+
+// Shared scratch of the Givens block of k_dcgs_b (in its dynamic shared memory).
+template <typename T> struct GivensScratch {
+    T R[SYLV_MR * SYLV_MAXV];
+    T col[SYLV_MAXV + 1];
+    T g[SYLV_MAXV];
+    T sn[SYLV_MR];
+    double cs[SYLV_MR];
+    double scale[SYLV_MAXV];
+};
+template <typename T, typename S, typename C> constexpr int dcgs_b_smem_bytes() {
+    return sweep_smem_bytes<S, C>() > (int)sizeof(GivensScratch<T>) ? sweep_smem_bytes<S, C>()
+                                                                    : (int)sizeof(GivensScratch<T>);
+}
+
+// Last block of system st in k_dcgs_a: beta, Hessenberg column j - 1 (first
+// pass + s, subdiagonal beta; its Givens update is left to k_dcgs_b), and
+// when the cycle can go on the coefficients of sweep b and the first pass of
+// column j.  The fields it reads are copied to shared memory in one burst of
+// asynchronous copies, issued together with the loads of the chunk reduction.
+template <typename T, typename S, typename C>
+__device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int j, double sj) {
+    extern __shared__ __align__(16) unsigned char sweep_dsm[];
+    SysState<T>& ss = *reinterpret_cast<SysState<T>*>(sweep_dsm);
+    __shared__ T tot[PSTRIDE];
+    __shared__ T s_s[SYLV_MAXV], s_z[SYLV_MAXV];
+    __shared__ double s_beta;
+    __shared__ T s_vy;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // scalars, scale and h1; formed columns 0..j-2 of H
+    const size_t ncol = (size_t)(j > 1 ? j - 1 : 0) * SYLV_MAXV * sizeof(T);
+    state_copy_async(st, &ss, 0, offsetof(SysState<T>, h2));
+    state_copy_async(st, &ss, offsetof(SysState<T>, Hr), offsetof(SysState<T>, Hr) + ncol);
+    cp_async_commit();
+    reduce_chunks(sd.part, sd.nchunks, PSTRIDE, 2 * j + 2, tot);
+    cp_async_wait<0>();
+    __syncthreads();
+    // s = V^* u_j (scaled), z = V^* y, beta = ||u_j - V s||: one warp, lane l < j
+    if (warp == 0) {
+        T sl = zero<T>(), zl = zero<T>();
+        if (lane < j) {
+            sl = (ss.scale[lane] * sj) * tot[lane];
+            zl = ss.scale[lane] * tot[j + lane];
+            s_s[lane] = sl;
+            s_z[lane] = zl;
+        }
+        const double nss = warp_sum(abs2(sl));
+        const T sz = warp_sum(conjg(sl) * zl);
+        if (lane == 0) {
+            const double alpha = sj * sj * re(tot[2 * j]);
+            const double beta = sqrt(fmax(alpha - nss, 0.0));
+            s_beta = beta;
+            s_vy = sdiv((double)sj * tot[2 * j + 1] - sz, make_scalar<T>(beta, 0.0));
+            st->counter = 0;
+        }
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    if (j >= 1) {
+        // Hessenberg column j - 1 as formed, for the Givens block and for the
+        // first pass of the next columns
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            const T v = i < j ? ss.h1[i] + s_s[i] : make_scalar<T>(beta, 0.0);
+            ss.Hr[(j - 1) * SYLV_MAXV + i] = v;
+            st->Hr[(j - 1) * SYLV_MAXV + i] = v;
+        }
+        if (threadIdx.x == 0) st->gpend = j;
+    }
+    // the cycle goes on unless the restart length is reached or beta is zero
+    // or not finite; the Givens block then ends it (j >= 1), else it ends here
+    const bool go = j < sd.restart && beta > 0.0 && isfinite(beta);
+    if (!go) {
+        if (threadIdx.x == 0) {
+            if (j == 0) {
+                if (!isfinite(beta)) st->status = ST_NONFINITE;
+                st->nvec = 0;
+                st->phase = PH_UPDATE;
+            }
+            st->upd = 0;
+        }
+        return;
+    }
+    __syncthreads();
+    // first pass of column j and the coefficients of sweep b
+    const double ib = 1.0 / beta;
+    const T vy = s_vy;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        T hs = zero<T>();                        // (H s)_i over the first j columns
+        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += ss.Hr[c * SYLV_MAXV + i] * s_s[c];
+        const T zi = i < j ? s_z[i] : vy;
+        st->h1[i] = ib * (zi - hs);
+    }
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        st->h2[l] = ss.scale[l] * s_s[l];      // v_j   = sj U - sum h2_l X_l
+        st->cz[l] = ss.scale[l] * s_z[l];      // u_j+1 = Y - sum cz_l X_l - cv X_j
+    }
+    if (threadIdx.x == 0) {
+        st->cv = ib * vy;
+        st->sjb = sj;
+        st->jb = j;
+        st->upd = 1;
+        st->scale[j] = ib;
+        st->scale[j + 1] = ib;
+        st->j = j + 1;
+    }
+}
+
+// Givens block of system st in k_dcgs_b: the pending Hessenberg column
+// c = gpend - 1 (formed in k_dcgs_a) gets the previous rotations and a new
+// one; g and the residual estimate are updated and the Arnoldi step is
+// counted; the cycle ends when the estimate meets the tolerance, the column
+// is the last of the restart length, the step cap is reached, the
+// subdiagonal is zero or a value is not finite.  At the end of a cycle the
+// least-squares solution y (back substitution, one warp) is formed and the
+// system moves to the update phase.
+template <typename T, typename S, typename C>
+__device__ void dcgs_givens(const SysDesc<T, S, C>& sd, SysState<T>* st) {
+    extern __shared__ __align__(16) unsigned char sweep_dsm[];
+    GivensScratch<T>& gs = *reinterpret_cast<GivensScratch<T>*>(sweep_dsm);
+    __shared__ int s_end, s_c;
+    if (threadIdx.x == 0) s_c = st->gpend - 1;
+    __syncthreads();
+    const int c = s_c;
+    if (c < 0) return;
+    for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) gs.col[i] = st->Hr[c * SYLV_MAXV + i];
+    for (int i = threadIdx.x; i <= c; i += blockDim.x) {
+        gs.g[i] = st->g[i];
+        gs.scale[i] = st->scale[i];
+        if (i < c) { gs.cs[i] = st->cs[i]; gs.sn[i] = st->sn[i]; }
+    }
+    for (int q = threadIdx.x; q < c * SYLV_MAXV; q += blockDim.x) gs.R[q] = st->R[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // previous rotations applied to the column, carried down its rows
+        T carry = gs.col[0];
+        for (int i = 0; i < c; ++i) {
+            const double cc_ = gs.cs[i];
+            const T sn_ = gs.sn[i];
+            const T nx = gs.col[i + 1];
+            const T t0 = cc_ * carry + sn_ * nx;
+            carry = cc_ * nx - conjg(sn_) * carry;
+            gs.R[c * SYLV_MAXV + i] = t0;
+            st->R[c * SYLV_MAXV + i] = t0;
+        }
+        const T hn = gs.col[c + 1];
+        const double hnr = re(hn);
+        double cr;
+        T sr;
+        givens(carry, hn, cr, sr);
+        st->cs[c] = cr;
+        st->sn[c] = sr;
+        const T rcc = cr * carry + sr * hn;
+        gs.R[c * SYLV_MAXV + c] = rcc;
+        st->R[c * SYLV_MAXV + c] = rcc;
+        const T gc = gs.g[c];
+        const T gc1 = -(conjg(sr) * gc);
+        st->g[c + 1] = gc1;
+        st->g[c] = cr * gc;
+        gs.g[c] = cr * gc;
+        const double est = absv(gc1);
+        const int iters = st->iters + 1;
+        st->est = est;
+        st->iters = iters;
+        if (sd.hist && iters - 1 < sd.hist_cap) sd.hist[iters - 1] = est;
+        int e;
+        if (!isfinite(est) || !isfinite(hnr)) {
+            st->status = ST_NONFINITE;
+            st->nvec = 0;
+            st->phase = PH_UPDATE;
+            e = 2;
+        } else if (est <= st->tol || c + 1 >= sd.restart || iters >= st->max_iters || hnr == 0.0) {
+            st->nvec = c + 1;
+            e = 1;
+        } else {
+            e = 0;
+        }
+        if (e != 0) st->upd = 0;
+        st->gpend = 0;
+        s_end = e;
+    }
+    __syncthreads();
+    if (s_end != 1 || threadIdx.x >= 32) return;
+    // end of the cycle: back substitution R y = g, lane l owns g[l]
+    const int lane = threadIdx.x;
+    const int k = c + 1;
+    T gl = lane < k ? gs.g[lane] : zero<T>();
+    T yl = zero<T>();
+    for (int i = k - 1; i >= 0; --i) {
+        const T num = shfl_idx(gl, i);
+        const T rii = gs.R[i * SYLV_MAXV + i];
+        const T yi = (absv(rii) != 0.0) ? sdiv(num, rii) : zero<T>();
+        if (lane == i) yl = yi;
+        if (lane < i) gl -= gs.R[i * SYLV_MAXV + lane] * yi;
+    }
+    if (lane < k) st->y[lane] = gs.scale[lane] * yl;
+    __syncwarp();
+    if (lane == 0) st->phase = PH_UPDATE;
 }
 
 template <typename T, typename S, typename C>
@@ -781,80 +1094,7 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     }
 #undef SYLV_DCGSA_CALL
     if (!last_block(&st->counter, sd.nchunks)) return;
-    // ---- the step's sequential part: one block per system ----
-    __shared__ T tot[PSTRIDE];
-    __shared__ T s_s[SYLV_MAXV], s_z[SYLV_MAXV], s_col[SYLV_MAXV];
-    __shared__ T s_H[SYLV_MR * SYLV_MAXV];      // Hessenberg columns 0..j-1 as formed
-    __shared__ T s_R[SYLV_MR * SYLV_MAXV];      // rotated columns (Givens scratch)
-    __shared__ double s_beta;
-    __shared__ T s_vy;
-    // the columns formed so far, in parallel (read below by the first pass of column j)
-    for (int q = threadIdx.x; q < (j > 0 ? (j - 1) * SYLV_MAXV : 0); q += blockDim.x) s_H[q] = st->Hr[q];
-    reduce_chunks(sd.part, sd.nchunks, PSTRIDE, 2 * j + 2, tot);
-    for (int l = threadIdx.x; l < j; l += blockDim.x) {
-        s_s[l] = (st->scale[l] * sj) * tot[l];
-        s_z[l] = st->scale[l] * tot[j + l];
-    }
-    if (threadIdx.x == 0) st->counter = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ss = 0.0;
-        for (int l = 0; l < j; ++l) ss += abs2(s_s[l]);
-        const double alpha = sj * sj * re(tot[2 * j]);
-        s_beta = sqrt(fmax(alpha - ss, 0.0));
-    }
-    __syncthreads();
-    const double beta = s_beta;
-    int end = 0;
-    if (j >= 1) {
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-            const T v = i < j ? st->h1[i] + s_s[i] : make_scalar<T>(beta, 0.0);
-            if (i < j) s_col[i] = v;
-            s_H[(j - 1) * SYLV_MAXV + i] = v;
-            st->Hr[(j - 1) * SYLV_MAXV + i] = v;
-        }
-        __syncthreads();
-        end = hess_column_finish<T>(sd.restart, sd.hist, sd.hist_cap, st, j - 1, s_col, beta, s_R);
-    } else if (!(beta > 0.0) || !isfinite(beta)) {
-        if (threadIdx.x == 0) {
-            if (!isfinite(beta)) st->status = ST_NONFINITE;
-            st->nvec = 0;
-            st->phase = PH_UPDATE;
-        }
-        end = 2;
-    }
-    if (end != 0) {
-        if (threadIdx.x == 0) st->upd = 0;
-        return;
-    }
-    // the cycle goes on: first pass of column j and the coefficients of sweep b
-    if (threadIdx.x == 0) {
-        T sz = zero<T>();
-        for (int l = 0; l < j; ++l) sz += conjg(s_s[l]) * s_z[l];
-        s_vy = sdiv((double)sj * tot[2 * j + 1] - sz, make_scalar<T>(beta, 0.0));
-    }
-    __syncthreads();
-    const double ib = 1.0 / beta;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        T hs = zero<T>();                        // (H s)_i over the first j columns
-        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += s_H[c * SYLV_MAXV + i] * s_s[c];
-        const T zi = i < j ? s_z[i] : s_vy;
-        st->h1[i] = ib * (zi - hs);
-    }
-    for (int l = threadIdx.x; l < j; l += blockDim.x) {
-        st->h2[l] = st->scale[l] * s_s[l];      // v_j   = sj U - sum h2_l X_l
-        st->cz[l] = st->scale[l] * s_z[l];      // u_j+1 = Y - sum cz_l X_l - cv X_j
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        st->cv = ib * s_vy;
-        st->sjb = sj;
-        st->jb = j;
-        st->upd = 1;
-        st->scale[j] = ib;
-        st->scale[j + 1] = ib;
-        st->j = j + 1;
-    }
+    dcgs_step_tail<T, S, C>(sd, st, j, sj);
 }
 
 // Rows [r0, r1) of sweep b: X_j <- sj U - sum_l a_l X_l, slot j+1 <- Y - sum_l c_l X_l - cv X_j.
@@ -894,12 +1134,20 @@ __device__ __forceinline__ void dcgs_b_rows(const SysDesc<T, S, C>& sd, int jb, 
     }
 }
 
+// Grid: nsys Givens blocks (block q < nsys serves system q), then one block
+// per work item for the sweep.
 template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_dcgs_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const Item* __restrict__ items,
-         BatchCtl* ctl) {
+         BatchCtl* ctl, int nsys) {
     count_launch(ctl, K_CGS3);
-    const Item it = items[blockIdx.x];
+    if ((int)blockIdx.x < nsys) {
+        SysState<T>* sg = sts + blockIdx.x;
+        if (sg->gpend > 0) dcgs_givens<T, S, C>(sysd[blockIdx.x], sg);
+        if (ctl->graph) graph_tail<T>(ctl, sts, K_CGS3);
+        return;
+    }
+    const Item it = items[blockIdx.x - nsys];
     SysState<T>* st = sts + it.sys;
     if (st->phase == PH_ARNOLDI && st->upd) {
         const SysDesc<T, S, C> sd = sysd[it.sys];
