@@ -277,6 +277,11 @@ struct SysState {
     int jb;
     int upd;
     int gpend;              // delayed CGS2: Hessenberg column gpend - 1 awaits its Givens update (0: none)
+    int h1pend;             // delayed CGS2: first pass of column h1pend - 1 still to form (0: none)
+    double fib;             // delayed CGS2, inputs of that first pass: 1 / beta,
+    T fvy;                  //   v_j^* y,
+    T fs[SYLV_MAXV];        //   s = V^* u_j (scaled),
+    T fz[SYLV_MAXV];        //   z = V^* y (scaled)
 };
 
 // Work item of a launch: (system, chunk).

@@ -3,6 +3,7 @@
 // shifts) in inst_real.cu and for cplx (complex shifts) in inst_cplx.cu.
 #pragma once
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "internal.h"
@@ -127,6 +128,9 @@ struct Engine {
     long long launches[K_COUNT] = {};   // all launches
     long long tick_no = 0;
     int prof_every = 4;
+    // host driver: programmatic dependent launches (off if unsupported or if
+    // the environment sets SYLV_NO_PDL)
+    int pdl = std::getenv("SYLV_NO_PDL") ? 0 : 1;
 
     ~Engine() {
         for (auto& e : ev)
@@ -210,6 +214,32 @@ struct Engine {
     // Blocks of the restart kernels (grid-stride over the work items).
     int restart_grid() const { return std::max(1, std::min(nitems, 2 * num_sms())); }
 
+    // A kernel of the device iteration, launched with programmatic stream
+    // serialization (the kernel waits for its predecessor in pdl_enter());
+    // if the launch with the attribute is refused, later launches go without.
+    template <typename... P, typename... A>
+    int launch(void (*kern)(P...), dim3 grid, size_t smem, A... args) {
+        const dim3 block(SYLV_BLOCK);
+        if (pdl) {
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = block;
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess) return SYLV_OK;
+            (void)cudaGetLastError();
+            pdl = 0;
+        }
+        kern<<<grid, block, smem, stream>>>(args...);
+        SYLV_CK(cudaGetLastError());
+        return SYLV_OK;
+    }
+
     // One device iteration: every active system advances one Arnoldi step
     // and restarts if its cycle ended.
     // With profiling on, every prof_every-th tick is bracketed by events.
@@ -228,11 +258,11 @@ struct Engine {
             return SYLV_OK;
         };
         if (ortho == 1 && cgs_mode == 0) {
-            k_dcgs_a<T, S, C><<<grid, block, dcgs_a_smem_bytes<T, S, C>(), stream>>>(d_sd.p, d_st.p, d_ops.p,
-                                                                                    d_items.p, d_ctl.p);
+            SYLV_TRY(launch(k_dcgs_a<T, S, C>, grid, dcgs_a_smem_bytes<T, S, C>(), d_sd.p, d_st.p, d_ops.p,
+                            d_items.p, d_ctl.p));
             SYLV_TRY(mark(K_SPMV));
-            k_dcgs_b<T, S, C><<<nitems + nsys, block, dcgs_b_smem_bytes<T, S, C>(), stream>>>(d_sd.p, d_st.p,
-                                                                                        d_items.p, d_ctl.p, nsys);
+            SYLV_TRY(launch(k_dcgs_b<T, S, C>, dim3(nitems + nsys), dcgs_b_smem_bytes<T, S, C>(), d_sd.p, d_st.p,
+                            d_items.p, d_ctl.p, nsys));
             SYLV_TRY(mark(K_CGS3));
         } else {
             k_arnoldi_spmv<T, S, C><<<grid, block, sm, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p, cgs_mode);
@@ -244,9 +274,9 @@ struct Engine {
         }
         if (cgs_mode == 0 && with_restart) {
             const dim3 rgrid(restart_grid());
-            k_restart_update<T, S, C><<<rgrid, block, 0, stream>>>(d_sd.p, d_st.p, d_items.p, d_ctl.p);
+            SYLV_TRY(launch(k_restart_update<T, S, C>, rgrid, 0, d_sd.p, d_st.p, d_items.p, d_ctl.p));
             SYLV_TRY(mark(K_RUPD));
-            k_restart_residual<T, S, C><<<rgrid, block, 0, stream>>>(d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p);
+            SYLV_TRY(launch(k_restart_residual<T, S, C>, rgrid, 0, d_sd.p, d_st.p, d_ops.p, d_items.p, d_ctl.p));
             SYLV_TRY(mark(K_RRES));
         }
         if (pe) pending[slot] = nk;
@@ -256,6 +286,7 @@ struct Engine {
 
     // Add the event-timed durations of a finished tick to the totals.
     int harvest(int slot) {
+        if (pending[slot]) SYLV_CK(cudaEventSynchronize(pev[slot][pending[slot]]));
         for (int q = 0; q < pending[slot]; ++q) {
             float ms = 0.f;
             SYLV_CK(cudaEventElapsedTime(&ms, pev[slot][q], pev[slot][q + 1]));
@@ -296,7 +327,11 @@ struct Engine {
     // its arithmetic does not change.
     int run(long long max_ticks) {
         const int D = 4;
-        long long t = 0;
+        // flow control: one event per G ticks (an event recorded between two
+        // kernels ends their programmatic overlap), at most D events (2 with
+        // programmatic launches, so about 8 ticks) in flight
+        const int G = pdl ? 4 : 1, DE = pdl ? 2 : D;
+        long long t = 0, grp = 0;
         while (*(volatile int*)h_flag != 0) {
             if (t >= max_ticks) {
                 set_error("inner solves did not finish within %lld device iterations", max_ticks);
@@ -305,9 +340,12 @@ struct Engine {
             const int slot = (int)(t % D);
             if (pending[slot]) SYLV_TRY(harvest(slot));
             SYLV_TRY(launch_tick(0, slot, restart_every <= 1 || t % restart_every == 0));
-            SYLV_CK(cudaEventRecord(ev[slot], stream));
             ++t;
-            if (t >= D) SYLV_CK(cudaEventSynchronize(ev[t % D]));
+            if (t % G == 0) {
+                SYLV_CK(cudaEventRecord(ev[grp % DE], stream));
+                ++grp;
+                if (grp >= DE) SYLV_CK(cudaEventSynchronize(ev[grp % DE]));
+            }
         }
         ticks += t;
         if (profile) {

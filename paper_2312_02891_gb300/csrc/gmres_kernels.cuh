@@ -48,18 +48,33 @@ __device__ __forceinline__ void block_reduce_store(A (&acc)[NV], int cnt, T* out
 }
 
 // True in exactly one block: the last of nchunks blocks to finish this launch.
+// The block's stores (its partial sums) are ordered before thread 0's
+// increment by the barrier; the increment is a release (for this block's
+// stores) and an acquire (for the stores of the blocks counted before it),
+// and the second barrier passes that on to the block's other threads, whose
+// loads of the partial sums bypass L1.  No thread of the block needs a full
+// fence of its own.
 __device__ __forceinline__ bool last_block(unsigned* counter, int nchunks) {
     __shared__ int am_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(counter, 1u);
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
         am_last = (prev == (unsigned)(nchunks - 1));
     }
     __syncthreads();
-    if (am_last) __threadfence();
     return am_last != 0;
 }
+
+// Programmatic dependent launch.  A kernel of the device iteration first
+// waits until the previous kernel of the stream has completed and its stores
+// are visible (a no-op when it was launched without the attribute, e.g. in a
+// graph).  The next kernel may be scheduled once every block of this one has
+// called pdl_trigger() or exited: k_dcgs_a triggers after its sweep, so the
+// blocks of k_dcgs_b take the SM slots freed during the sequential tail and
+// start the moment it ends; the other kernels trigger by exiting.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // tot[l] = sum over chunks c of part[c * stride + l], l < cnt, in a fixed
 // order.  Thread t takes sum l = t mod W and the chunks c = g, g + G, ...
@@ -868,9 +883,11 @@ template <typename T, typename S, typename C> constexpr int dcgs_a_smem_bytes() 
 // Shared scratch of the Givens block of k_dcgs_b (in its dynamic shared memory).
 template <typename T> struct GivensScratch {
     T R[SYLV_MR * SYLV_MAXV];
+    T H[SYLV_MR * SYLV_MAXV];
     T col[SYLV_MAXV + 1];
     T g[SYLV_MAXV];
     T sn[SYLV_MR];
+    T fs[SYLV_MAXV];
     double cs[SYLV_MR];
     double scale[SYLV_MAXV];
 };
@@ -881,22 +898,21 @@ template <typename T, typename S, typename C> constexpr int dcgs_b_smem_bytes() 
 
 // Last block of system st in k_dcgs_a: beta, Hessenberg column j - 1 (first
 // pass + s, subdiagonal beta; its Givens update is left to k_dcgs_b), and
-// when the cycle can go on the coefficients of sweep b and the first pass of
-// column j.  The fields it reads are copied to shared memory in one burst of
-// asynchronous copies, issued together with the loads of the chunk reduction.
+// when the cycle can go on the coefficients of sweep b (the first pass of
+// column j is also left to k_dcgs_b).  The fields it reads are copied to
+// shared memory in one burst of asynchronous copies, issued together with the
+// loads of the chunk reduction.
 template <typename T, typename S, typename C>
 __device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int j, double sj) {
     extern __shared__ __align__(16) unsigned char sweep_dsm[];
     SysState<T>& ss = *reinterpret_cast<SysState<T>*>(sweep_dsm);
     __shared__ T tot[PSTRIDE];
     __shared__ T s_s[SYLV_MAXV], s_z[SYLV_MAXV];
-    __shared__ double s_beta;
+    __shared__ double s_beta, s_ib;
     __shared__ T s_vy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // scalars, scale and h1; formed columns 0..j-2 of H
-    const size_t ncol = (size_t)(j > 1 ? j - 1 : 0) * SYLV_MAXV * sizeof(T);
+    // scalars, scale and h1
     state_copy_async(st, &ss, 0, offsetof(SysState<T>, h2));
-    state_copy_async(st, &ss, offsetof(SysState<T>, Hr), offsetof(SysState<T>, Hr) + ncol);
     cp_async_commit();
     reduce_chunks(sd.part, sd.nchunks, PSTRIDE, 2 * j + 2, tot);
     cp_async_wait<0>();
@@ -913,10 +929,14 @@ __device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int 
         const double nss = warp_sum(abs2(sl));
         const T sz = warp_sum(conjg(sl) * zl);
         if (lane == 0) {
+            // beta and 1 / beta from one reciprocal square root (the float64
+            // square root and divisions are long dependent sequences here)
             const double alpha = sj * sj * re(tot[2 * j]);
-            const double beta = sqrt(fmax(alpha - nss, 0.0));
-            s_beta = beta;
-            s_vy = sdiv((double)sj * tot[2 * j + 1] - sz, make_scalar<T>(beta, 0.0));
+            const double x = fmax(alpha - nss, 0.0);
+            const double rs = x > 0.0 ? rsqrt(x) : 0.0;
+            s_beta = x * rs;
+            s_ib = rs;
+            s_vy = ((double)sj * tot[2 * j + 1] - sz) * rs;
             st->counter = 0;
         }
     }
@@ -925,11 +945,8 @@ __device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int 
     if (j >= 1) {
         // Hessenberg column j - 1 as formed, for the Givens block and for the
         // first pass of the next columns
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-            const T v = i < j ? ss.h1[i] + s_s[i] : make_scalar<T>(beta, 0.0);
-            ss.Hr[(j - 1) * SYLV_MAXV + i] = v;
-            st->Hr[(j - 1) * SYLV_MAXV + i] = v;
-        }
+        for (int i = threadIdx.x; i <= j; i += blockDim.x)
+            st->Hr[(j - 1) * SYLV_MAXV + i] = i < j ? ss.h1[i] + s_s[i] : make_scalar<T>(beta, 0.0);
         if (threadIdx.x == 0) st->gpend = j;
     }
     // the cycle goes on unless the restart length is reached or beta is zero
@@ -946,19 +963,14 @@ __device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int 
         }
         return;
     }
-    __syncthreads();
-    // first pass of column j and the coefficients of sweep b
-    const double ib = 1.0 / beta;
+    // the coefficients of sweep b, and the inputs of the first pass of column j
+    const double ib = s_ib;
     const T vy = s_vy;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        T hs = zero<T>();                        // (H s)_i over the first j columns
-        for (int c = (i > 0 ? i - 1 : 0); c < j; ++c) hs += ss.Hr[c * SYLV_MAXV + i] * s_s[c];
-        const T zi = i < j ? s_z[i] : vy;
-        st->h1[i] = ib * (zi - hs);
-    }
     for (int l = threadIdx.x; l < j; l += blockDim.x) {
         st->h2[l] = ss.scale[l] * s_s[l];      // v_j   = sj U - sum h2_l X_l
         st->cz[l] = ss.scale[l] * s_z[l];      // u_j+1 = Y - sum cz_l X_l - cv X_j
+        st->fs[l] = s_s[l];
+        st->fz[l] = s_z[l];
     }
     if (threadIdx.x == 0) {
         st->cv = ib * vy;
@@ -968,35 +980,48 @@ __device__ void dcgs_step_tail(const SysDesc<T, S, C>& sd, SysState<T>* st, int 
         st->scale[j] = ib;
         st->scale[j + 1] = ib;
         st->j = j + 1;
+        st->fib = ib;
+        st->fvy = vy;
+        st->h1pend = j + 1;
     }
 }
 
-// Givens block of system st in k_dcgs_b: the pending Hessenberg column
-// c = gpend - 1 (formed in k_dcgs_a) gets the previous rotations and a new
-// one; g and the residual estimate are updated and the Arnoldi step is
+// Givens block of system st in k_dcgs_b.  Warp 0: the pending Hessenberg
+// column c = gpend - 1 (formed in k_dcgs_a) gets the previous rotations and a
+// new one; g and the residual estimate are updated and the Arnoldi step is
 // counted; the cycle ends when the estimate meets the tolerance, the column
 // is the last of the restart length, the step cap is reached, the
 // subdiagonal is zero or a value is not finite.  At the end of a cycle the
-// least-squares solution y (back substitution, one warp) is formed and the
-// system moves to the update phase.
+// least-squares solution y is formed (back substitution, one warp) and the
+// system moves to the update phase.  Warps 1..7 meanwhile form the first
+// pass of the new column jn = h1pend - 1, h1 = (z - H s) / beta over the
+// formed columns 0..jn-1 (four lanes per row), which the next k_dcgs_a
+// completes.
 template <typename T, typename S, typename C>
 __device__ void dcgs_givens(const SysDesc<T, S, C>& sd, SysState<T>* st) {
     extern __shared__ __align__(16) unsigned char sweep_dsm[];
     GivensScratch<T>& gs = *reinterpret_cast<GivensScratch<T>*>(sweep_dsm);
-    __shared__ int s_end, s_c;
-    if (threadIdx.x == 0) s_c = st->gpend - 1;
-    __syncthreads();
-    const int c = s_c;
-    if (c < 0) return;
-    for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) gs.col[i] = st->Hr[c * SYLV_MAXV + i];
-    for (int i = threadIdx.x; i <= c; i += blockDim.x) {
-        gs.g[i] = st->g[i];
-        gs.scale[i] = st->scale[i];
-        if (i < c) { gs.cs[i] = st->cs[i]; gs.sn[i] = st->sn[i]; }
-    }
-    for (int q = threadIdx.x; q < c * SYLV_MAXV; q += blockDim.x) gs.R[q] = st->R[q];
-    __syncthreads();
+    __shared__ int s_end, s_c, s_jn;
     if (threadIdx.x == 0) {
+        s_c = st->gpend - 1;
+        s_jn = st->h1pend - 1;
+    }
+    __syncthreads();
+    const int c = s_c, jn = s_jn;
+    // column c of H and the rotation state (c >= 0); formed columns 0..jn-1 (jn >= 1)
+    if (c >= 0) {
+        for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) gs.col[i] = st->Hr[c * SYLV_MAXV + i];
+        for (int i = threadIdx.x; i <= c; i += blockDim.x) {
+            gs.g[i] = st->g[i];
+            gs.scale[i] = st->scale[i];
+            if (i < c) { gs.cs[i] = st->cs[i]; gs.sn[i] = st->sn[i]; }
+        }
+        for (int q = threadIdx.x; q < c * SYLV_MAXV; q += blockDim.x) gs.R[q] = st->R[q];
+    }
+    for (int q = threadIdx.x; q < (jn > 0 ? jn : 0) * SYLV_MAXV; q += blockDim.x) gs.H[q] = st->Hr[q];
+    for (int q = threadIdx.x; q < jn; q += blockDim.x) gs.fs[q] = st->fs[q];
+    __syncthreads();
+    if (threadIdx.x == 0 && c >= 0) {
         // previous rotations applied to the column, carried down its rows
         T carry = gs.col[0];
         for (int i = 0; i < c; ++i) {
@@ -1043,18 +1068,35 @@ __device__ void dcgs_givens(const SysDesc<T, S, C>& sd, SysState<T>* st) {
         if (e != 0) st->upd = 0;
         st->gpend = 0;
         s_end = e;
+    } else if (threadIdx.x == 0) {
+        s_end = 0;
+    }
+    if (jn >= 0 && threadIdx.x >= 32) {
+        // first pass of column jn: row i = (t - 32) / 4, columns c' = part, part + 4, ...
+        const int t = threadIdx.x - 32, i = t >> 2, part = t & 3;
+        T hs = zero<T>();
+        if (i <= jn)
+            for (int q = (i > 0 ? i - 1 : 0) + part; q < jn; q += 4) hs += gs.H[q * SYLV_MAXV + i] * gs.fs[q];
+        hs += shfl_xor(hs, 1);
+        hs += shfl_xor(hs, 2);
+        if (part == 0 && i <= jn) {
+            const T zi = i < jn ? st->fz[i] : st->fvy;
+            st->h1[i] = st->fib * (zi - hs);
+        }
+        if (t == 0) st->h1pend = 0;
     }
     __syncthreads();
     if (s_end != 1 || threadIdx.x >= 32) return;
-    // end of the cycle: back substitution R y = g, lane l owns g[l]
+    // end of the cycle: back substitution R y = g, lane l owns g[l]; the
+    // reciprocals of the diagonal are formed first, in parallel
     const int lane = threadIdx.x;
     const int k = c + 1;
     T gl = lane < k ? gs.g[lane] : zero<T>();
+    const T rll = lane < k ? gs.R[lane * SYLV_MAXV + lane] : zero<T>();
+    const T rinv = absv(rll) != 0.0 ? sdiv(make_scalar<T>(1.0, 0.0), rll) : zero<T>();
     T yl = zero<T>();
     for (int i = k - 1; i >= 0; --i) {
-        const T num = shfl_idx(gl, i);
-        const T rii = gs.R[i * SYLV_MAXV + i];
-        const T yi = (absv(rii) != 0.0) ? sdiv(num, rii) : zero<T>();
+        const T yi = shfl_idx(gl, i) * shfl_idx(rinv, i);
         if (lane == i) yl = yi;
         if (lane < i) gl -= gs.R[i * SYLV_MAXV + lane] * yi;
     }
@@ -1069,6 +1111,7 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
          const Item* __restrict__ items, BatchCtl* ctl) {
     typedef typename RealOf<C>::type CR;
     __shared__ T red[SYLV_NWARP][PSTRIDE];
+    pdl_wait();
     count_launch(ctl, K_SPMV);
     if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ctl->h_loop, 0u);
     const Item it = items[blockIdx.x];
@@ -1093,6 +1136,7 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         SYLV_BUCKET_SWITCH(j - 1, SYLV_DCGSA_CALL)
     }
 #undef SYLV_DCGSA_CALL
+    pdl_trigger();
     if (!last_block(&st->counter, sd.nchunks)) return;
     dcgs_step_tail<T, S, C>(sd, st, j, sj);
 }
@@ -1140,10 +1184,11 @@ template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK, SweepOcc<C>::value)
 k_dcgs_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const Item* __restrict__ items,
          BatchCtl* ctl, int nsys) {
+    pdl_wait();
     count_launch(ctl, K_CGS3);
     if ((int)blockIdx.x < nsys) {
         SysState<T>* sg = sts + blockIdx.x;
-        if (sg->gpend > 0) dcgs_givens<T, S, C>(sysd[blockIdx.x], sg);
+        if (sg->gpend > 0 || sg->h1pend > 0) dcgs_givens<T, S, C>(sysd[blockIdx.x], sg);
         if (ctl->graph) graph_tail<T>(ctl, sts, K_CGS3);
         return;
     }
@@ -1214,6 +1259,7 @@ template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK)
 k_restart_update(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
                  const Item* __restrict__ items, BatchCtl* ctl) {
+    pdl_wait();
     count_launch(ctl, K_RUPD);
     const int ni = ctl->nitems;
     for (int q = blockIdx.x; q < ni; q += gridDim.x) {
@@ -1287,6 +1333,7 @@ template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK)
 k_restart_residual(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
                    const OpDesc* __restrict__ ops, const Item* __restrict__ items, BatchCtl* ctl) {
+    pdl_wait();
     count_launch(ctl, K_RRES);
     const int ni = ctl->nitems;
     for (int q = blockIdx.x; q < ni; q += gridDim.x) {
