@@ -17,13 +17,15 @@ controller  eqs. (ADI_relax1_prak), (upd_resgap), (ADI_relax2_prak),
 gmres       restarted GMRES(m) with right Jacobi preconditioning, the inner
             solver of the shifted systems (Sec. 3.3 "Further implementation
             aspects": per-column solves, ||r(:,l)|| <= delta_k / r).
-lradi       Algorithm 1 (inexact LR-ADI) with direct or GMRES inner solves.
+lradi       Algorithm 1 (inexact LR-ADI) with direct or GMRES inner solves,
+            for eq. (sylv) and (with M, C) the generalized eq. (gsylv).
 residual    exact norms through low-rank factors: ||w t^*||, the true
             residual of eq. (adi_res_inexact), differences of factored X.
 dense       the plain definition of the solution of eq. (sylv): Kronecker
             solve and Bartels-Stewart (scipy), for pinning on small inputs.
 
-Pins: every function is checked in tests/test_oracle_*.py against closed
+Pins: every function is checked in tests/test_oracle_*.py (the
+generalized path in tests/test_oracle_generalized.py) against closed
 forms, dense solves, the identities of Theorems 1 and 2, and the bound of
 Theorem 3.  Functions without such a pin say "parity unpinned" in their
 docstring.

@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Solves (Op + sigma I) x = b for one column b, the inner systems of
 Algorithm 1: (A + beta_k I) z = w_{k-1}(:, l) and (B^T + conj(alpha_k) I)
-y = t_{k-1}(:, l).  The paper's guidance for the inner solver (Sec. 3.3,
+y = t_{k-1}(:, l); with a mass matrix, (Op + sigma Mass) x = b, the systems
+(A + beta_k M) z = w_{k-1}(:, l) and (B + alpha_k C)^* y = t_{k-1}(:, l) of
+the generalized equation (eq. (lradi_g), Algorithm 1).  The paper's guidance for the inner solver (Sec. 3.3,
 "Further implementation aspects"):
 
 * each of the r columns is solved separately, to ||r(:,l)|| <= delta_k / r;
@@ -119,23 +121,25 @@ def arnoldi_dcgs2(apply, v0, k):
     return V, H, napply
 
 
-def shifted_apply(S, sigma, x):
-    """(Op + sigma I) x."""
-    return S @ x + sigma * x
+def shifted_apply(S, sigma, x, mass=None):
+    """(Op + sigma I) x, or (Op + sigma Mass) x with a mass matrix."""
+    return S @ x + sigma * (x if mass is None else mass @ x)
 
 
 def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
-          jacobi: bool = False, ortho: str = "cgs2") -> GmresResult:
+          jacobi: bool = False, ortho: str = "cgs2", mass=None) -> GmresResult:
     """GMRES(restart) for (S + sigma I) x = b, stop when ||b - (S+sigma I)x|| <= tol.
 
-    S is a scipy sparse matrix, sigma a real or complex scalar.  With
+    S is a scipy sparse matrix, sigma a real or complex scalar; with a
+    (sparse) mass matrix the system is (S + sigma Mass) x = b.  With
     jacobi=True the method runs on (S + sigma I) P^{-1} u = b with
-    P = diag(S) + sigma I and returns x = P^{-1} u.
+    P = diag(S) + sigma I (diag(S) + sigma diag(Mass)) and returns x = P^{-1} u.
     """
     dtype = np.result_type(S.dtype, np.asarray(sigma).dtype, b.dtype)
     n = b.shape[0]
     b = b.astype(dtype)
-    pinv = 1.0 / (S.diagonal().astype(dtype) + sigma) if jacobi else np.ones(n, dtype)
+    dmass = 1.0 if mass is None else mass.diagonal().astype(dtype)
+    pinv = 1.0 / (S.diagonal().astype(dtype) + sigma * dmass) if jacobi else np.ones(n, dtype)
     x = np.zeros(n, dtype)
     r = b.copy()
     beta = np.linalg.norm(r)
@@ -145,7 +149,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
         return GmresResult(x, beta, 0, 0, True, hist)
     m = restart
     if ortho == "dcgs2":
-        return _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype)
+        return _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass)
     while True:
         cycles += 1
         V = np.zeros((m + 1, n), dtype)
@@ -157,7 +161,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
         V[0] = r / beta
         j_done = 0
         for j in range(m):
-            w = shifted_apply(S, sigma, pinv * V[j])
+            w = shifted_apply(S, sigma, pinv * V[j], mass)
             iters += 1
             h = np.zeros(j + 2, dtype)
             if ortho == "mgs":
@@ -194,7 +198,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
             acc = g[i] - R[i, i + 1: k] @ y[i + 1: k]
             y[i] = acc / R[i, i] if R[i, i] != 0 else 0.0
         x = x + pinv * (V[:k].T @ y)
-        r = b - shifted_apply(S, sigma, x)
+        r = b - shifted_apply(S, sigma, x, mass)
         beta = np.linalg.norm(r)
         if beta <= tol:
             return GmresResult(x, beta, iters, cycles, True, hist)
@@ -202,7 +206,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
             return GmresResult(x, beta, iters, cycles, False, hist)
 
 
-def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype) -> GmresResult:
+def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None) -> GmresResult:
     """The restarted GMRES above with the Arnoldi steps of arnoldi_dcgs2.
 
     Column j-1 of the Hessenberg matrix is complete once step j has the
@@ -230,7 +234,7 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype) -> GmresResult:
         h1 = None
         k = 0
         for j in range(m + 1):
-            y = shifted_apply(S, sigma, pinv * u) if j < m else None
+            y = shifted_apply(S, sigma, pinv * u, mass) if j < m else None
             s = V[:j].conj() @ u
             alpha = np.vdot(u, u).real
             beta = np.sqrt(max(alpha - np.vdot(s, s).real, 0.0))
@@ -267,7 +271,7 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype) -> GmresResult:
             acc = g[i] - R[i, i + 1: k] @ y_[i + 1: k]
             y_[i] = acc / R[i, i] if R[i, i] != 0 else 0.0
         x = x + pinv * (V[:k].T @ y_)
-        r = b - shifted_apply(S, sigma, x)
+        r = b - shifted_apply(S, sigma, x, mass)
         beta0 = np.linalg.norm(r)
         if beta0 <= tol:
             return GmresResult(x, beta0, iters, cycles, True, hist)

@@ -1,19 +1,21 @@
-"""Algorithm 1 (inexact LR-ADI for Sylvester equations), M = I, C = I.
+"""Algorithm 1 (inexact LR-ADI for Sylvester equations).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Solves A X + X B = -f g^* (eq. (sylv)) for X ~ Z Gamma Y^*, following the
-steps of Algorithm 1 in the paper's order:
+Solves A X + X B = -f g^* (eq. (sylv)), or with nonsingular M, C the
+generalized equation A X C + M X B = -f g^* (eq. (gsylv)), for
+X ~ Z Gamma Y^*, following the steps of Algorithm 1 in the paper's order
+(M = I, C = I when they are not given):
 
   w_0 = f, t_0 = g, Z = Y = Gamma = [], k = 1
   while ||w_{k-1} t_{k-1}^*|| >= tau ||f g^*||:
       (delta^A_k, delta^B_k) from the controller (Sec. 3.3)
-      solve (A + beta_k I) z_k = w_{k-1}      to ||r^A_k|| <= delta^A_k
-      solve (B + alpha_k I)^* y_k = t_{k-1}   to ||r^B_k|| <= delta^B_k
+      solve (A + beta_k M) z_k = w_{k-1}      to ||r^A_k|| <= delta^A_k
+      solve (B + alpha_k C)^* y_k = t_{k-1}   to ||r^B_k|| <= delta^B_k
       gamma_k = -(beta_k + alpha_k)
-      w_k = w_{k-1} + gamma_k z_k,  t_k = t_{k-1} + conj(gamma_k) y_k
+      w_k = w_{k-1} + gamma_k M z_k,  t_k = t_{k-1} + conj(gamma_k) C^* y_k
       Z = [Z, z_k], Y = [Y, y_k], Gamma = diag(Gamma, gamma_k I_r)
-      u_k, v_k by eq. (upd_resgap)
+      u_k, v_k by eq. (upd_resgap) (with ||M z_k||, ||C^T y_k||)
       k = k + 1
 
 Readings where the paper is silent or inconsistent:
@@ -85,7 +87,7 @@ def _is_pair_start(alpha, beta, idx):
     return np.conj(a) == alpha[idx + 1] and np.conj(b) == beta[idx + 1]
 
 
-def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, **opts) -> LradiResult:
+def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) -> LradiResult:
     o = dict(DEFAULTS)
     unknown = set(opts) - set(o)
     if unknown:
@@ -98,7 +100,9 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, **opts) -> LradiResult:
     if o["fixed_tol"] is None:
         o["fixed_tol"] = tau / 20
     SA = _as_scipy(A)
-    SBt = _as_scipy(B).T.tocsr()            # (B + alpha I)^* = B^T + conj(alpha) I for real B
+    SBt = _as_scipy(B).T.tocsr()            # (B + alpha C)^* = B^T + conj(alpha) C^T for real B, C
+    SM = None if M is None else _as_scipy(M)
+    SCt = None if C is None else _as_scipy(C).conj().T.tocsr()
     alpha = np.asarray(alpha)
     beta = np.asarray(beta)
     cplx = np.iscomplexobj(alpha) or np.iscomplexobj(beta) or np.iscomplexobj(f)
@@ -143,31 +147,35 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, **opts) -> LradiResult:
             if o["inner"] == "direct":
                 key = ("A", complex(b_k))
                 if key not in lu_cache:
-                    lu_cache[key] = spla.splu((SA + b_k * sp.eye(n)).astype(dt).tocsc())
+                    mA = sp.eye(n) if SM is None else SM
+                    lu_cache[key] = spla.splu((SA + b_k * mA).astype(dt).tocsc())
                 z[:, l] = lu_cache[key].solve(w[:, l])
                 key = ("B", complex(a_k))
                 if key not in lu_cache:
-                    lu_cache[key] = spla.splu((SBt + np.conj(a_k) * sp.eye(m)).astype(dt).tocsc())
+                    mB = sp.eye(m) if SCt is None else SCt
+                    lu_cache[key] = spla.splu((SBt + np.conj(a_k) * mB).astype(dt).tocsc())
                 y[:, l] = lu_cache[key].solve(t[:, l])
             else:
                 ra = gmres(SA, b_k, w[:, l], dA / r, o["restart"], o["max_inner"],
-                           o["jacobi"], o["ortho"])
+                           o["jacobi"], o["ortho"], mass=SM)
                 rb = gmres(SBt, np.conj(a_k), t[:, l], dB / r, o["restart"], o["max_inner"],
-                           o["jacobi"], o["ortho"])
+                           o["jacobi"], o["ortho"], mass=SCt)
                 z[:, l], y[:, l] = ra.x, rb.x
                 itsA += ra.iters; itsB += rb.iters
                 okA &= ra.converged; okB &= rb.converged
-        rA = w - (SA @ z + b_k * z)
-        rB = t - (SBt @ y + np.conj(a_k) * y)
+        Mz = z if SM is None else SM @ z
+        Cy = y if SCt is None else SCt @ y          # C^* y
+        rA = w - (SA @ z + b_k * Mz)
+        rB = t - (SBt @ y + np.conj(a_k) * Cy)
         gam = -(b_k + a_k)
-        w = w + gam * z
-        t = t + np.conj(gam) * y
+        w = w + gam * Mz
+        t = t + np.conj(gam) * Cy
         Zs.append(z); Ys.append(y); gammas.extend([gam] * r)
         if o["keep_inner_residuals"]:
             SAs.append(rA); SBs.append(rB)
         nrA, nrB = block_norm2(rA), block_norm2(rB)
-        u = u + abs(gam) * block_norm2(z) * nrB
-        v = v + abs(gam) * block_norm2(y) * nrA
+        u = u + abs(gam) * block_norm2(Mz) * nrB
+        v = v + abs(gam) * block_norm2(Cy) * nrA
         itsA_tot += itsA; itsB_tot += itsB
         res = lowrank_norm2(w, t)
         hist.append(dict(k=k, alpha=a_k, beta=b_k, dA=dA, dB=dB, eps_hat=eh, nrA=nrA, nrB=nrB,

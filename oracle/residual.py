@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 * ||w t^*||_2, the computed residual norm of eq. (adi_resexact), via thin QR
   of both factors (||Q_w R_w R_t^* Q_t^*|| = ||R_w R_t^*||).
 * The true Sylvester residual of eq. (adi_res_inexact),
-  R = A Z Gamma Y^* + Z Gamma Y^* B + f g^*  (M = C = I),
-  factored as U W^* with U = [A Z, Z, f], W = [Y Gamma^*, B^* Y Gamma^*, g];
+  R = A Z Gamma Y^* C + M Z Gamma Y^* B + f g^*  (M = C = I unless given),
+  factored as U W^* with U = [A Z, M Z, f], W = [C^* Y Gamma^*, B^* Y Gamma^*, g];
   its exact 2-norm replaces the paper's a-posteriori eigs estimate (Sec. 4).
 * Frobenius norm of the difference of two factored solutions.
 """
@@ -37,11 +37,12 @@ def lowrank_fro(U: np.ndarray, W: np.ndarray) -> float:
     return float(np.linalg.norm(Ru @ Rw.conj().T, "fro"))
 
 
-def true_residual_norm2(A, B, f, g, Z, gamma, Y) -> float:
-    """||A X + X B + f g^*||_2 for X = Z diag(gamma) Y^* (eq. adi_res_inexact)."""
+def true_residual_norm2(A, B, f, g, Z, gamma, Y, M=None, C=None) -> float:
+    """||A X C + M X B + f g^*||_2 for X = Z diag(gamma) Y^* (eq. adi_res_inexact;
+    M = C = I when not given)."""
     Yg = Y * np.conj(gamma)[None, :]
-    U = np.hstack([A @ Z, Z, f])
-    W = np.hstack([Yg, B.conj().T @ Yg, g])
+    U = np.hstack([A @ Z, Z if M is None else M @ Z, f])
+    W = np.hstack([Yg if C is None else C.conj().T @ Yg, B.conj().T @ Yg, g])
     return lowrank_norm2(U, W)
 
 

@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "CSR", "normal", "convdiff", "rhs_factors", "ritz_values",
     "inverse_ritz_values", "select_shift_pairs", "Problem", "make_problem",
-    "problem_config", "batch_problems",
+    "problem_config", "batch_problems", "mass_matrix", "make_problem_g",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -149,6 +149,29 @@ def convdiff(N: int, dim: int, kind: str, mag: float) -> CSR:
     return CSR(n, rowptr.astype(np.int32), cidx.astype(np.int32), v.astype(np.float64))
 
 
+def _csr_from_scipy(S) -> CSR:
+    S = S.tocsr()
+    S.sort_indices()
+    return CSR(S.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+def mass_matrix(N: int, dim: int) -> CSR:
+    """Consistent mass matrix of Q1 (bilinear / trilinear) finite elements on
+    the uniform grid of convdiff (N interior nodes per dimension, Dirichlet
+    boundary, same node ordering): the Kronecker product of the 1D P1 mass
+    matrices (h/6) tridiag(1, 4, 1); symmetric positive definite, 9 (2D) or
+    27 (3D) nonzeros per interior row."""
+    import scipy.sparse as sp
+    if dim not in (2, 3):
+        raise ValueError("dim must be 2 or 3")
+    h = 1.0 / (N + 1)
+    M1 = sp.diags([np.full(N - 1, h / 6), np.full(N, 4 * h / 6), np.full(N - 1, h / 6)], [-1, 0, 1])
+    M = M1
+    for _ in range(dim - 1):
+        M = sp.kron(M1, M)          # x fastest: the first factor is the slowest index
+    return _csr_from_scipy(M)
+
+
 def rhs_factors(n: int, m: int, r: int, seed: int):
     """f (n x r), g (m x r): N(0,1) columns, each factor rescaled to unit 2-norm.
 
@@ -197,6 +220,21 @@ def inverse_ritz_values(op: CSR, steps: int = 20) -> np.ndarray:
     mu = _arnoldi_ritz(lu.solve, op.n, steps)
     mu = mu[np.abs(mu) > 0]
     return 1.0 / mu
+
+
+def generalized_ritz_values(op: CSR, mass: CSR, steps: int = 20) -> np.ndarray:
+    """Ritz and inverse Ritz values of the pencil (op, mass), i.e. of
+    mass^{-1} op and of op^{-1} mass (sparse LU applied): the spectrum
+    Lambda(A, M) that replaces Lambda(A) in the shift problem of the
+    generalized equation (Sec. 2, after eq. (lradi_g))."""
+    import scipy.sparse.linalg as spla
+    S, Mm = op.to_scipy(), mass.to_scipy()
+    lum = spla.splu(Mm.tocsc())
+    lus = spla.splu(S.tocsc())
+    ritz = _arnoldi_ritz(lambda x: lum.solve(S @ x), op.n, steps)
+    mu = _arnoldi_ritz(lambda x: lus.solve(Mm @ x), op.n, steps)
+    mu = mu[np.abs(mu) > 0]
+    return np.concatenate([ritz, 1.0 / mu])
 
 
 def select_shift_pairs(cand_a: np.ndarray, cand_b: np.ndarray, count: int,
@@ -317,7 +355,8 @@ def select_real_shifts_sampled(cand_a, cand_b, count: int, grids=(0, 12, 25, 50,
 
 @dataclass
 class Problem:
-    """One Sylvester instance A X + X B = -f g^* with shifts and options."""
+    """One Sylvester instance A X + X B = -f g^* (or, with M and C, the
+    generalized A X C + M X B = -f g^* of eq. (gsylv)) with shifts and options."""
     name: str
     A: CSR
     B: CSR
@@ -327,6 +366,8 @@ class Problem:
     beta: np.ndarray
     tau: float = 1e-8
     opts: dict = field(default_factory=dict)
+    M: CSR | None = None
+    C: CSR | None = None
 
     @property
     def r(self) -> int:
@@ -364,6 +405,30 @@ def make_problem(name, NA, dimA, kindA, magA, NB, dimB, kindB, magB, r, seed,
     return Problem(name, A, B, f, g, alpha, beta, tau, dict(opts))
 
 
+def make_problem_g(name, NA, dimA, kindA, magA, NB, dimB, kindB, magB, r, seed, n_shifts,
+                   tau=1e-8, ritz_steps=20, **opts) -> Problem:
+    """A generalized instance A X C + M X B = -f g^* shaped like a finite
+    element discretisation (the paper's Ex. 4 is a finite element model whose
+    data is not available): M, C consistent Q1 mass matrices, A = h^d A_fd and
+    B = h^d B_fd the convection-diffusion operators of convdiff scaled like
+    stiffness matrices, so that Lambda(A, M), Lambda(B, C) lie close to
+    Lambda(A_fd), Lambda(B_fd).  Real shift pairs from the Ritz and inverse
+    Ritz values of the pencils."""
+    hA = (1.0 / (NA + 1)) ** dimA
+    hB = (1.0 / (NB + 1)) ** dimB
+    Afd = convdiff(NA, dimA, kindA, magA)
+    Bfd = convdiff(NB, dimB, kindB, magB)
+    A = CSR(Afd.n, Afd.rowptr, Afd.colind, Afd.val * hA)
+    B = CSR(Bfd.n, Bfd.rowptr, Bfd.colind, Bfd.val * hB)
+    M = mass_matrix(NA, dimA)
+    C = mass_matrix(NB, dimB)
+    f, g = rhs_factors(A.n, B.n, r, seed)
+    cand_a = generalized_ritz_values(A, M, ritz_steps)
+    cand_b = generalized_ritz_values(B, C, ritz_steps)
+    alpha, beta = select_shift_pairs(cand_a, cand_b, n_shifts, real=True)
+    return Problem(name, A, B, f, g, alpha, beta, tau, dict(opts), M, C)
+
+
 def problem_config(which: str) -> Problem:
     """Named workloads shaped like the paper's experiments.
 
@@ -381,7 +446,16 @@ def problem_config(which: str) -> Problem:
       right-Jacobi GMRES(20).
     * "small3d": A 3D N=24, omega=100(1,1,1); B 3D N=20, omega=50(z,x,y);
       r=4, seed 4, 8 complex shift pairs (test size of the 3D family).
+    * "tiny2d_g", "small2d_g": the generalized equation (make_problem_g) on
+      the grids and fields of "tiny2d" / "small2d" (seeds 8, 5), 8 / 12 real
+      shift pairs of the pencils.
     """
+    if which == "tiny2d_g":
+        return make_problem_g("tiny2d_g", 12, 2, "xy", 10.0, 10, 2, "rot2", 5.0, 2, 8, 8,
+                              restart=30, jacobi=False)
+    if which == "small2d_g":
+        return make_problem_g("small2d_g", 32, 2, "xy", 10.0, 30, 2, "rot2", 5.0, 1, 5, 12,
+                              restart=30, jacobi=True)
     if which == "mid3d":
         return make_problem("mid3d", 128, 3, "const3", 100.0, 100, 3, "zxy", 50.0, 4, 2, 16,
                             real_shifts=False, restart=30, jacobi=True)
