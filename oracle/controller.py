@@ -69,19 +69,39 @@ def select_prefer_B(eps_hat, N_w, N_t, dmin_A, dmax_A, dmin_B, dmax_B):
     return dA, dB
 
 
+def select_direct(direct, eps_hat, N_w, N_t, dmin_A, dmax_A, dmin_B, dmax_B):
+    """Sec. 3.3 "Combination of direct and iterative linear solves": the
+    systems of one side are solved directly (||r|| ~ 0 there), and the
+    criteria reduce to ||r^B_k|| <= hat-eps_k / ||w_{k-1}|| (A direct) or
+    ||r^A_k|| <= hat-eps_k / ||t_{k-1}|| (B direct), the points of the
+    admissible curve of eq. (tolBfromtolA) at delta = 0 on the direct side,
+    clamped as in eq. (bound_tols).  The direct side's tolerance is 0."""
+    if direct == "A":
+        return 0.0, max(min(tol_B_from_A(eps_hat, 0.0, N_w, N_t), dmax_B), dmin_B)
+    if direct == "B":
+        return max(min(tol_A_from_B(eps_hat, 0.0, N_w, N_t), dmax_A), dmin_A), 0.0
+    raise ValueError(f"direct side must be 'A' or 'B', not {direct!r}")
+
+
 def inner_tolerances(strategy: str, *, k: int, kmax: int, eps: float, xi: float,
                      u_prev: float, v_prev: float, N_w: float, N_t: float,
                      dmin_A: float, dmax_A: float, dmin_B: float, dmax_B: float,
-                     fixed_tol: float):
-    """(delta^A_k, delta^B_k, hat-eps_k) for outer step k (1-based)."""
+                     fixed_tol: float, direct: str | None = None):
+    """(delta^A_k, delta^B_k, hat-eps_k) for outer step k (1-based).  With
+    direct = "A" or "B" the systems of that side are solved directly and
+    select_direct replaces the strategy's selection rule (its hat-eps rule
+    is kept)."""
     if strategy not in STRATEGIES:
         raise ValueError(f"unknown strategy {strategy!r}")
     if strategy == "fixed":
-        return fixed_tol, fixed_tol, float("nan")
+        return (0.0 if direct == "A" else fixed_tol), (0.0 if direct == "B" else fixed_tol), float("nan")
     if strategy.startswith("bl_"):
         eh = eps_hat_bl(eps, k, kmax, u_prev, v_prev, xi)
     else:
         eh = eps_hat_nobl(eps, kmax, xi)
+    if direct is not None:
+        dA, dB = select_direct(direct, eh, N_w, N_t, dmin_A, dmax_A, dmin_B, dmax_B)
+        return dA, dB, eh
     side = strategy.split("_")[1]
     sel = {"mid": select_mid, "A": select_prefer_A, "B": select_prefer_B}[side]
     dA, dB = sel(eh, N_w, N_t, dmin_A, dmax_A, dmin_B, dmax_B)

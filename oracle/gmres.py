@@ -277,3 +277,64 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None) -> Gmre
             return GmresResult(x, beta0, iters, cycles, True, hist)
         if iters >= max_iters:
             return GmresResult(x, beta0, iters, cycles, False, hist)
+
+
+def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = False,
+             mass=None) -> GmresResult:
+    """BiCGstab (van der Vorst, SIAM J. Sci. Stat. Comput. 13 (1992)) for
+    (S + sigma I) x = b, or (S + sigma Mass) x = b, with right Jacobi
+    preconditioning: the short-recurrence inner solver the paper uses for
+    its unsymmetric systems (Sec. 3.3 "Further implementation aspects",
+    Sec. 4).  Right preconditioning keeps the recurrence residual that of the
+    original system; after termination the true residual is recomputed and,
+    if it is not below tol, the method starts again from the current iterate
+    (fresh shadow vector).  iters counts BiCGstab steps (two operator
+    applications each); history holds the recurrence residual norms.  A
+    breakdown (rho or the step denominator zero) restarts the same way."""
+    dtype = np.result_type(S.dtype, np.asarray(sigma).dtype, b.dtype)
+    n = b.shape[0]
+    b = b.astype(dtype)
+    dmass = 1.0 if mass is None else mass.diagonal().astype(dtype)
+    pinv = 1.0 / (S.diagonal().astype(dtype) + sigma * dmass) if jacobi else np.ones(n, dtype)
+    x = np.zeros(n, dtype)
+    r = b.copy()
+    rn = np.linalg.norm(r)
+    hist = []
+    iters = cycles = 0
+    while rn > tol and iters < max_iters:
+        cycles += 1
+        rhat = r.copy()
+        rho = alpha = omega = 1.0
+        v = np.zeros(n, dtype)
+        p = np.zeros(n, dtype)
+        while iters < max_iters:
+            rho_new = np.vdot(rhat, r)
+            if rho_new == 0.0 or omega == 0.0:
+                break
+            beta = (rho_new / rho) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            ph = pinv * p
+            v = shifted_apply(S, sigma, ph, mass)
+            den = np.vdot(rhat, v)
+            iters += 1
+            if den == 0.0:
+                break
+            alpha = rho_new / den
+            s = r - alpha * v
+            if np.linalg.norm(s) <= tol:
+                x = x + alpha * ph
+                hist.append(np.linalg.norm(s))
+                break
+            sh = pinv * s
+            t = shifted_apply(S, sigma, sh, mass)
+            tt = np.vdot(t, t).real
+            omega = np.vdot(t, s) / tt if tt > 0.0 else 0.0
+            x = x + alpha * ph + omega * sh
+            r = s - omega * t
+            rho = rho_new
+            hist.append(np.linalg.norm(r))
+            if hist[-1] <= tol:
+                break
+        r = b - shifted_apply(S, sigma, x, mass)
+        rn = np.linalg.norm(r)
+    return GmresResult(x, rn, iters, cycles, rn <= tol, hist)

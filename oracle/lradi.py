@@ -34,6 +34,12 @@ Readings where the paper is silent or inconsistent:
   skipped after the first member of a pair.
 * An inner solve that reaches its iteration cap keeps its best iterate and
   its achieved residual feeds u, v.
+* Inner solvers: "direct" (sparse LU), "gmres" (restarted GMRES, right
+  Jacobi) or "bicgstab" (the paper's short-recurrence choice, right Jacobi),
+  for both sides (inner) or per side (inner_A, inner_B).  When exactly one
+  side is direct, its tolerance is 0 and the other side's follows the
+  simplified rule of Sec. 3.3 ("Combination of direct and iterative linear
+  solves"): ||r|| <= hat-eps_k / ||w_{k-1}|| (or / ||t_{k-1}||).
 """
 from __future__ import annotations
 
@@ -44,10 +50,10 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import controller as ctl
-from .gmres import gmres
+from .gmres import bicgstab, gmres
 from .residual import block_norm2, lowrank_norm2
 
-DEFAULTS = dict(strategy="bl_mid", inner="gmres", restart=30, max_inner=20000,
+DEFAULTS = dict(strategy="bl_mid", inner="gmres", inner_A=None, inner_B=None, restart=30, max_inner=20000,
                 jacobi=False, xi=1.0, dmin_A=None, dmin_B=None, dmax_A=0.1,
                 dmax_B=0.1, kmax=50, fixed_tol=None, ortho="cgs2",
                 keep_inner_residuals=False)
@@ -87,6 +93,12 @@ def _is_pair_start(alpha, beta, idx):
     return np.conj(a) == alpha[idx + 1] and np.conj(b) == beta[idx + 1]
 
 
+def _iterative(solver, S, sigma, b, tol, o, mass):
+    if solver == "gmres":
+        return gmres(S, sigma, b, tol, o["restart"], o["max_inner"], o["jacobi"], o["ortho"], mass=mass)
+    return bicgstab(S, sigma, b, tol, o["max_inner"], o["jacobi"], mass=mass)
+
+
 def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) -> LradiResult:
     o = dict(DEFAULTS)
     unknown = set(opts) - set(o)
@@ -99,6 +111,16 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) ->
         o["dmin_B"] = tau / 20
     if o["fixed_tol"] is None:
         o["fixed_tol"] = tau / 20
+    solver_A = o["inner_A"] or o["inner"]
+    solver_B = o["inner_B"] or o["inner"]
+    for sv in (solver_A, solver_B):
+        if sv not in ("direct", "gmres", "bicgstab"):
+            raise ValueError(f"unknown inner solver {sv!r}")
+    direct_side = None
+    if solver_A == "direct" and solver_B != "direct":
+        direct_side = "A"
+    elif solver_B == "direct" and solver_A != "direct":
+        direct_side = "B"
     SA = _as_scipy(A)
     SBt = _as_scipy(B).T.tocsr()            # (B + alpha C)^* = B^T + conj(alpha) C^T for real B, C
     SM = None if M is None else _as_scipy(M)
@@ -138,31 +160,34 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) ->
         dA, dB, eh = ctl.inner_tolerances(
             o["strategy"], k=k, kmax=o["kmax"], eps=eps, xi=o["xi"], u_prev=u, v_prev=v,
             N_w=N_w, N_t=N_t, dmin_A=o["dmin_A"], dmax_A=o["dmax_A"],
-            dmin_B=o["dmin_B"], dmax_B=o["dmax_B"], fixed_tol=o["fixed_tol"])
+            dmin_B=o["dmin_B"], dmax_B=o["dmax_B"], fixed_tol=o["fixed_tol"], direct=direct_side)
         z = np.zeros((n, r), dt)
         y = np.zeros((m, r), dt)
         itsA = itsB = 0
         okA = okB = True
         for l in range(r):
-            if o["inner"] == "direct":
+            if solver_A == "direct":
                 key = ("A", complex(b_k))
                 if key not in lu_cache:
                     mA = sp.eye(n) if SM is None else SM
                     lu_cache[key] = spla.splu((SA + b_k * mA).astype(dt).tocsc())
                 z[:, l] = lu_cache[key].solve(w[:, l])
+            else:
+                ra = _iterative(solver_A, SA, b_k, w[:, l], dA / r, o, SM)
+                z[:, l] = ra.x
+                itsA += ra.iters
+                okA &= ra.converged
+            if solver_B == "direct":
                 key = ("B", complex(a_k))
                 if key not in lu_cache:
                     mB = sp.eye(m) if SCt is None else SCt
                     lu_cache[key] = spla.splu((SBt + np.conj(a_k) * mB).astype(dt).tocsc())
                 y[:, l] = lu_cache[key].solve(t[:, l])
             else:
-                ra = gmres(SA, b_k, w[:, l], dA / r, o["restart"], o["max_inner"],
-                           o["jacobi"], o["ortho"], mass=SM)
-                rb = gmres(SBt, np.conj(a_k), t[:, l], dB / r, o["restart"], o["max_inner"],
-                           o["jacobi"], o["ortho"], mass=SCt)
-                z[:, l], y[:, l] = ra.x, rb.x
-                itsA += ra.iters; itsB += rb.iters
-                okA &= ra.converged; okB &= rb.converged
+                rb = _iterative(solver_B, SBt, np.conj(a_k), t[:, l], dB / r, o, SCt)
+                y[:, l] = rb.x
+                itsB += rb.iters
+                okB &= rb.converged
         Mz = z if SM is None else SM @ z
         Cy = y if SCt is None else SCt @ y          # C^* y
         rA = w - (SA @ z + b_k * Mz)

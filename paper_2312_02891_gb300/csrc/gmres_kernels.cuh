@@ -5,13 +5,19 @@
 // ||r(:, l)|| <= delta_k / r (Sec. 3.3, "Further implementation aspects").
 //
 // One launch serves every active system of a batch: the grid is a list of
-// (system, chunk) work items, each chunk a contiguous row range.  An Arnoldi
-// step is three sweeps over the rows (classical Gram-Schmidt applied twice):
+// (system, chunk) work items, each chunk a contiguous row range.  With
+// classical Gram-Schmidt applied twice an Arnoldi step is three sweeps over
+// the rows:
 //   k_arnoldi_spmv : w = (Op + sigma I) P^{-1} v_j and h1 = V^* w (fused)
 //   k_cgs_pass2    : h2 = V^* (w - V h1)
 //   k_cgs_pass3    : v_{j+1} = w - V (h1 + h2), ||v_{j+1}||, then the Givens
 //                    update of the Hessenberg least-squares problem
-// and a restart is two more:
+// and with the second pass delayed by one step (DCGS2) two:
+//   k_dcgs_a : the product and every dot product of the step; the last
+//              block of each system forms beta and the coefficients of sweep b
+//   k_dcgs_b : the basis update, beside one Givens block per system (Givens
+//              update, stop test, first pass of the next column);
+// a restart is two more:
 //   k_restart_update   : x += P^{-1} V y
 //   k_restart_residual : r = b - (Op + sigma I) x in float64, ||r||, decision.
 // Chunk partial sums are reduced by the last block of each system to finish
