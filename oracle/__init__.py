@@ -19,6 +19,9 @@ gmres       restarted GMRES(m) with right Jacobi preconditioning, the inner
             aspects": per-column solves, ||r(:,l)|| <= delta_k / r).
 lradi       Algorithm 1 (inexact LR-ADI) with direct or GMRES inner solves,
             for eq. (sylv) and (with M, C) the generalized eq. (gsylv).
+lradi_real  Algorithm 1 with a real double step per complex conjugate shift
+            pair (Sec. 3.3 "Complex shift parameters"): one complex solve per
+            pair and side, real factors Z, Gamma, Y.
 residual    exact norms through low-rank factors: ||w t^*||, the true
             residual of eq. (adi_res_inexact), differences of factored X.
 dense       the plain definition of the solution of eq. (sylv): Kronecker
