@@ -93,7 +93,15 @@ typedef struct sylv_opts {
     int32_t driver;              /* 0: each solve is one CUDA graph whose conditional nodes
                                     the kernels set (no host round trip inside a solve);
                                     1: the host launches every device iteration.  Profiling
-                                    (sylv_adi_profile) always uses the host-driven loop. */
+                                    (sylv_adi_profile) always uses the host-driven loop.
+                                    The host-driven loop launches the kernels of an iteration
+                                    with programmatic stream serialization (each kernel waits
+                                    for its predecessor on the device; the next one is
+                                    scheduled early), falling back to plain launches if the
+                                    attribute is refused; the environment variable
+                                    SYLV_NO_PDL, when set, selects plain launches (results
+                                    are the same; profilers that cannot follow programmatic
+                                    launches need it). */
     int32_t ortho;               /* Arnoldi orthogonalisation of the inner GMRES:
                                     SYLV_ORTHO_CGS2: classical Gram-Schmidt twice, three
                                     sweeps over the basis and three reductions per step;
