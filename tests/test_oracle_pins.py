@@ -230,6 +230,31 @@ def test_controller_constants():
     assert ctl.eps_hat_bl(1e-8, 1, 50, 1e-9, 0.0) > 0
 
 
+def test_back_looking_target_beyond_the_first_step():
+    """eq. (ADI_relax2_prak) at k > 1 with u, v > 0, under and over budget.
+
+    c = 2 + sqrt(2) = 3.414213562373095, so 2 c kmax = 341.4213562373095 for
+    kmax = 50 and 136.5685424949238 for kmax = 20; the budget is
+    xi k eps / (2 c kmax) and hat-eps = |budget - u - v| / c."""
+    # k = 10, eps = 1e-8, xi = 1, u = 1e-11, v = 2e-11 (under budget):
+    # budget = 1e-7 / 341.4213562373095 = 2.9289321881345246e-10,
+    # budget - u - v = 2.6289321881345246e-10, / c = 7.699964106250138e-11
+    assert ctl.eps_hat_bl(1e-8, 10, 50, 1e-11, 2e-11) == pytest.approx(7.699964106250138e-11, rel=1e-13)
+    # k = 2, u = 5e-11, v = 3e-11 (over budget): budget = 2e-8 / 341.42... =
+    # 5.85786437626905e-11, budget - u - v = -2.14213562373095e-11; the
+    # literal |.| gives 2.14213562373095e-11 / c = 6.2741699796952045e-12
+    assert ctl.eps_hat_bl(1e-8, 2, 50, 5e-11, 3e-11) == pytest.approx(6.2741699796952045e-12, rel=1e-12)
+    # xi = 0.5, k = 4, kmax = 20, eps = 2e-9, u = 1e-12, v = 0:
+    # budget = 0.5 * 4 * 2e-9 / 136.5685424949238 = 2.928932188134525e-11,
+    # minus 1e-12 = 2.828932188134525e-11, / c = 8.285750543877043e-12
+    assert ctl.eps_hat_bl(2e-9, 4, 20, 1e-12, 0.0, xi=0.5) == pytest.approx(8.285750543877043e-12, rel=1e-13)
+    # the same through the controller entry point, which feeds eq. (simple_tols)
+    _, _, eh = ctl.inner_tolerances("bl_mid", k=10, kmax=50, eps=1e-8, xi=1.0, u_prev=1e-11, v_prev=2e-11,
+                                    N_w=1.0, N_t=1.0, dmin_A=1e-12, dmax_A=0.1, dmin_B=1e-12, dmax_B=0.1,
+                                    fixed_tol=5e-10)
+    assert eh == pytest.approx(7.699964106250138e-11, rel=1e-13)
+
+
 def test_fig1_axis_values():
     """Fig. 1 (c = 3, eps = 1e-8, ||t|| = 1e-5, ||w|| = 2e-3): the curve
     Psi = 0 meets the axes at eps/(c ||w||) and eps/(c ||t||)."""
