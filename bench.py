@@ -49,6 +49,8 @@ def parse():
                          "Krylov basis and sweeps, float64 outer iteration)")
     ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"],
                     help="Arnoldi orthogonalisation of the inner GMRES (all runs of the line)")
+    ap.add_argument("--inner", default="gmres", choices=["gmres", "bicgstab"],
+                    help="inner solver of the headline solve")
     ap.add_argument("--kmax", type=int, default=50,
                     help="outer step cap (a small value gives a short case for profilers)")
     ap.add_argument("--cpu-sample-its", type=int, default=60)
@@ -249,6 +251,7 @@ def run_ours(a):
     def make(**kw):
         kw.setdefault("kmax", a.kmax)
         kw.setdefault("ortho", a.ortho)
+        kw.setdefault("inner", a.inner)
         return P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, stream=stream,
                               jacobi=jac, restart=rst, **kw)
 
@@ -356,7 +359,11 @@ def run_ours(a):
                 # one CUDA graph per solve, device-set conditional nodes (no kernel events)
                 ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 3, False),
                 ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False),
-                ("fp32_cgs2", dict(strategy=a.strategy, precision="fp32", ortho="cgs2"), 1, 2, True)):
+                ("fp32_cgs2", dict(strategy=a.strategy, precision="fp32", ortho="cgs2"), 1, 2, True),
+                ("fp32_bicgstab", dict(strategy=a.strategy, precision="fp32", inner="bicgstab"), 1, 3, True),
+                ("fp64_bicgstab", dict(strategy=a.strategy, precision="fp64", inner="bicgstab"), 1, 2, True),
+                ("fp32_bicgstab_graph", dict(strategy=a.strategy, precision="fp32", inner="bicgstab", driver=0),
+                 1, 3, False)):
             sv = make(**kw)
             tv, stv = timed(sv, w_, k_, profile=prof)
             variants[name], _, vst = summary(sv, tv, stv)
@@ -377,9 +384,12 @@ def run_ours(a):
 
         # ---- batched workload: 64 independent 2D instances in one device loop ----
         probs = batch_future.result() if batch_future is not None else []
-        for prec, orth in ((("fp32", "cgs2"), ("fp32", "dcgs2"), ("fp64", "cgs2")) if probs else ()):
+        for prec, orth in ((("fp32", "cgs2"), ("fp32", "dcgs2"), ("fp64", "cgs2"), ("fp32", "bicgstab"))
+                           if probs else ()):
+            inner = "bicgstab" if orth == "bicgstab" else "gmres"
             with P.SylvesterADIBatch(probs, stream=stream, strategy=a.strategy, precision=prec, jacobi=1,
-                                     restart=30, ortho=orth) as bt:
+                                     restart=30, ortho="cgs2" if inner == "bicgstab" else orth,
+                                     inner=inner) as bt:
                 nsolve = 0
                 bt.solve()
                 nsolve += 1

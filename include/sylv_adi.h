@@ -75,7 +75,7 @@ typedef struct sylv_shift { double re, im; } sylv_shift;
 /* Solver options; sylv_opts_default() fills the paper's defaults (Sec. 4):
  * xi = 1, delta_min = tau/20 (set at create when left <= 0), delta_max = 0.1,
  * kmax = 50, strategy BL_MID, fixed_tol = tau/20 (when <= 0), GMRES(30),
- * max_inner = 20000, float64, right Jacobi on. */
+ * max_inner = 20000, float64, right Jacobi on, inner = SYLV_INNER_GMRES. */
 typedef struct sylv_opts {
     double  xi;                  /* safeguard xi in (0, 1] of eqs. (ADI_relax1/2_prak) */
     double  dmin_A, dmin_B;      /* eq. (bound_tols) lower clamps; <= 0 means tau/20 */
@@ -116,7 +116,28 @@ typedef struct sylv_opts {
                                     are the same, idle launches fewer (measured on the 2D
                                     benchmark workload: 1.59 s -> 1.45 s).  The graph driver
                                     launches them only when a cycle has ended. */
+    int32_t inner;               /* inner solver of the shifted systems (Sec. 3.3 "Further
+                                    implementation aspects": any Krylov method whose residual
+                                    norm is available, right preconditioned):
+                                    SYLV_INNER_GMRES: restarted GMRES(restart), ortho as above;
+                                    SYLV_INNER_BICGSTAB: BiCGstab (van der Vorst 1992), the
+                                    short-recurrence solver of the paper's experiments (Sec. 4):
+                                    no Krylov basis, two products per step; restart and ortho
+                                    are unused and precision SYLV_PREC_BF16 is not built (there
+                                    is no basis to store) */
+    int32_t real_pairs;          /* complex shifts only: 0: the complex formulation (two complex
+                                    steps per conjugate pair, complex factors, as the paper's
+                                    experiments keep it); 1: the real double step per conjugate
+                                    pair (Sec. 3.3 "Complex shift parameters"): one complex solve
+                                    per column for a side whose shift is complex (the second
+                                    solution follows from the first), two real-shift solves for a
+                                    side whose shift is real, real factors Z, Y and a real core
+                                    with 2 x 2 blocks (sylv_adi_core).  Runs the host-driven loop;
+                                    not built for batches with complex shifts. */
 } sylv_opts;
+
+#define SYLV_INNER_GMRES     0
+#define SYLV_INNER_BICGSTAB  1
 
 #define SYLV_ORTHO_CGS2  0
 #define SYLV_ORTHO_DCGS2 1
@@ -158,12 +179,20 @@ int sylv_opts_default(sylv_opts* o);
 /* ------------------------------------------------------------------------ */
 
 /* Upload a CSR matrix (or its transpose, transpose = 1) as a device operator.
- * A matrix whose nonzeros lie on at most 8 fixed diagonals (finite-difference
+ * A matrix whose nonzeros lie on at most 9 fixed diagonals (finite-difference
  * stencils, Sec. 4 eq. (ex:convdiff)) is stored by diagonals so the product
  * reads no column indices; any other CSR is kept as CSR.  The main diagonal is
  * kept for the Jacobi preconditioner.  Errors: SYLV_ERR_INVALID for a
  * malformed CSR (non-square, rowptr not monotone, column out of range). */
 int sylv_op_create(const sylv_csr* csr, int32_t transpose, sylv_op** out);
+/* The same for the shifted operators of the generalized equation
+ * A X C + M X B = -f g^* (eq. (gsylv), Algorithm 1 with M, C): Op + sigma Mass
+ * with a mass matrix of the same size (mass = NULL: Mass = I).  Both are
+ * stored by diagonals when their nonzeros together lie on at most 9 fixed
+ * offsets (the 2D finite element mass matrices of the Q1 elements), else as
+ * two CSR matrices.  transpose = 1 stores Op^T and Mass^T.  The Jacobi
+ * preconditioner becomes P = diag(Op) + sigma diag(Mass). */
+int sylv_op_create_g(const sylv_csr* csr, const sylv_csr* mass, int32_t transpose, sylv_op** out);
 /* Storage format chosen: 1 = by diagonals (*ndiag set), 0 = CSR. */
 int sylv_op_format(const sylv_op* op, int32_t* is_stencil, int32_t* ndiag, int32_t* n);
 /* Y = (Op + sigma I) P^{-1} X for ncols columns (device pointers, n x ncols,
@@ -198,12 +227,14 @@ int sylv_cgs2(const void* V, int32_t n, int32_t k, void* w, void* h_out,
  * sylv_cgs2.  1 <= k <= 30 and n <= sylv_cgs2_noalloc_max_rows().
  * Scratch lives in one static device array of SYLV_NOALLOC_SCRATCH_BYTES
  * that every GPU loading this library holds until the process exits; no
- * cudaMalloc/cudaFree or other allocating call is made.  The first call on
- * a device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture.  All
- * calls share the array and each call re-initialises what it reads, so calls
- * that overlap on the GPU (other streams, other host threads) race: serialise
- * them.  Sizes beyond the limit return SYLV_ERR_INVALID with a message. */
+ * cudaMalloc/cudaFree or other allocating call is made.  Each call looks up
+ * that array's device address on the current device, copies its small
+ * descriptors from host memory and synchronises the stream before it
+ * returns: the call is synchronous and must not be made while its stream is
+ * being captured into a CUDA graph.  All calls share the array and each call
+ * re-initialises what it reads, so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them.  Sizes beyond the
+ * limit return SYLV_ERR_INVALID with a message. */
 #define SYLV_NOALLOC_SCRATCH_BYTES (1 << 20)
 int sylv_cgs2_noalloc(double* V, int32_t n, int32_t k, const double* w, double* h_out, void* stream);
 /* Largest n sylv_cgs2_noalloc accepts. */
@@ -230,6 +261,39 @@ int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_c
                const void* B, void* X, int32_t ncols, double tol, int32_t restart,
                int32_t max_iters, int32_t precision, int32_t* iters_out, double* resnorm_out,
                double* hist_out, void* stream);
+
+/* One Arnoldi cycle of k steps (1 <= k <= SYLV_MAX_RESTART) of the inner
+ * GMRES exactly as the solver runs it (steps a2-a4): the operator
+ * (Op + sigma I) P^{-1} (right Jacobi when jacobi = 1), the Krylov basis in
+ * the storage and sweep precision of precision (SYLV_PREC_*), classical
+ * Gram-Schmidt twice (ortho = SYLV_ORTHO_CGS2) or with the second pass
+ * delayed (SYLV_ORTHO_DCGS2), from the unit start vector v0 (device, n
+ * entries).  Outputs: V_out (device, n x (k + 1), column-major) the basis
+ * vectors v_0..v_k (with DCGS2 the cycle does not complete v_k: that column
+ * is zero), H_out (host, (k + 1) x k, column-major) the Hessenberg matrix as
+ * formed, with Op' V_k = V_{k+1} H.  Values are float64 (complex128 when
+ * is_complex).  SYLV_ERR_NONFINITE if the cycle ended early (breakdown). */
+int sylv_arnoldi(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex, const void* v0,
+                 int32_t k, int32_t precision, int32_t ortho, void* V_out, void* H_out, void* stream);
+
+/* Solve (Op + sigma I) x_l = b_l for l = 0..ncols-1 by BiCGstab (van der
+ * Vorst, SIAM J. Sci. Stat. Comput. 13, 1992; the inner solver of the paper's
+ * experiments, Sec. 4) with x0 = 0, right Jacobi when jacobi = 1.  Each
+ * column stops when its recurrence residual (||s|| or ||r||) is <= tol, at a
+ * breakdown (rhat^* v = 0, rho = 0 or omega = 0) or after max_iters steps;
+ * the true residual ||b_l - (Op + sigma I) x_l|| is then recomputed in
+ * float64 and, if it is above tol, a new cycle starts from x with a fresh
+ * shadow vector rhat = r.  Arguments and outputs as sylv_gmres (iters_out
+ * counts BiCGstab steps, two operator applications each; hist_out the
+ * recurrence residual norm after each step).  The columns of one call share
+ * each launch, with the operator read once per row for up to four columns.
+ * precision = SYLV_PREC_FP64 or SYLV_PREC_FP32 (vectors and products in
+ * float32, x and the restart residual in float64).  Returns
+ * SYLV_ERR_INNER_STALL if a column stopped at max_iters. */
+int sylv_bicgstab(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+                  const void* B, void* X, int32_t ncols, double tol, int32_t max_iters,
+                  int32_t precision, int32_t* iters_out, double* resnorm_out, double* hist_out,
+                  void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Inner-tolerance controller (step a1), evaluated by the device code         */
@@ -258,6 +322,18 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
                     int32_t r, const sylv_shift* alpha, const sylv_shift* beta,
                     int32_t n_shifts, double tol, const sylv_opts* opts, void* stream,
                     sylv_handle** out);
+/* The generalized equation A X C + M X B = -f g^* (eq. (gsylv)) with
+ * nonsingular M (n x n) and C (m x m); M = NULL or C = NULL means identity.
+ * Algorithm 1 as printed: inner systems (A + beta_k M) z = w_{k-1} and
+ * (B + alpha_k C)^* y = t_{k-1}, updates w_k = w_{k-1} + gamma_k M z_k and
+ * t_k = t_{k-1} + conj(gamma_k) C^* y_k (eq. (lradi_g)), and the residual-gap
+ * estimate of eq. (upd_resgap) with ||M z_k||, ||C^T y_k||; X = Z Gamma Y^*
+ * as before.  Other arguments, errors and ownership as sylv_adi_create;
+ * SYLV_ERR_UNSUPPORTED with real_pairs = 1 and complex shifts. */
+int sylv_adi_create_g(const sylv_csr* A, const sylv_csr* B, const sylv_csr* M, const sylv_csr* C,
+                      const double* f, const double* g, int32_t r, const sylv_shift* alpha,
+                      const sylv_shift* beta, int32_t n_shifts, double tol, const sylv_opts* opts,
+                      void* stream, sylv_handle** out);
 /* Replace f and g (same shapes) before the next solve; host pointers. */
 int sylv_adi_set_rhs(sylv_handle* h, const double* f, const double* g);
 /* Same, from device pointers (n x r and m x r float64, column-major). */
@@ -276,6 +352,15 @@ int sylv_adi_history(const sylv_handle* h, double* buf, int32_t cap, int32_t* ro
 int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_t on_device,
                      int32_t* kr_out, int32_t* is_complex);
 int sylv_adi_destroy(sylv_handle* h);
+/* The real core of X = Z G Y^T when the factors are real (real shifts, or
+ * real_pairs = 1): G is kr x kr (host, column-major, leading dimension
+ * ld >= kr), diagonal for plain steps (gamma_k I_r) and with a 2 x 2 block
+ * P diag(gamma, conj gamma) Q^* (kron I_r) per conjugate pair.  G may be NULL
+ * to query kr.  With complex factors (the complex formulation) the core is
+ * the diagonal returned by sylv_adi_factors and this call returns
+ * SYLV_ERR_UNSUPPORTED.  With real_pairs = 1, sylv_adi_factors returns real
+ * Z, Y and must be given gamma = NULL. */
+int sylv_adi_core(const sylv_handle* h, double* G, int32_t ld, int32_t* kr_out);
 
 /* Kernel statistics of a handle.  SYLV_NUM_KERNELS entries, in this order:
  * shifted product + first Gram-Schmidt sweep, second sweep, third sweep with
@@ -315,11 +400,14 @@ typedef struct sylv_batch sylv_batch;
 
 /* Every instance runs Algorithm 1 with the same options (opts may be NULL;
  * dmin and fixed_tol defaults follow each instance's tol).  The 2 r_i column
- * systems of all instances share each GMRES sweep launch and instances move
- * between outer steps independently, so a solve is one CUDA graph launch with
- * no host round trip (opts->driver is ignored).  If any instance has complex
- * shifts the whole batch runs in complex arithmetic.  Pointers are borrowed
- * for the call.  Errors as sylv_adi_create, the message naming the instance. */
+ * systems of all instances share each sweep launch and instances move
+ * between outer steps independently.  opts->driver = 0: a solve is one CUDA
+ * graph launch with no host round trip; 1: the host launches every device
+ * iteration (outer kernel, step set-up, inner kernels) and reads a mapped
+ * word that the device clears when the last instance finishes (used while
+ * profiling).  If any instance has complex shifts the whole batch runs in
+ * complex arithmetic.  Pointers are borrowed for the call.  Errors as
+ * sylv_adi_create, the message naming the instance. */
 int sylv_adi_batch_create(int32_t count, const sylv_problem* probs, const sylv_opts* opts, void* stream,
                           sylv_batch** out);
 /* Solve all instances (blocks until done).  SYLV_OK when every instance
@@ -336,6 +424,14 @@ int sylv_adi_batch_factors(const sylv_batch* b, int32_t i, void* Z, void* Y, voi
  * of the last solve; algorithmic bytes and flops of all kernels. */
 int sylv_adi_batch_stats(const sylv_batch* b, int64_t* launches, double* bytes, double* flops,
                          int64_t* ticks);
+/* Replace instance i's f (n_i x r_i) and g (m_i x r_i), host pointers,
+ * before the next solve. */
+int sylv_adi_batch_set_rhs(sylv_batch* b, int32_t i, const double* f, const double* g);
+/* As sylv_adi_profile / sylv_adi_kernel_stats for the whole batch (the
+ * outer-step counter holds the batch's outer kernel, the step counter its
+ * set-up kernel); profiling runs the host-driven loop. */
+int sylv_adi_batch_profile(sylv_batch* b, int32_t enable);
+int sylv_adi_batch_kernel_stats(const sylv_batch* b, double* ms, double* bytes, double* flops, int64_t* launches);
 int sylv_adi_batch_destroy(sylv_batch* b);
 
 #ifdef __cplusplus

@@ -17,14 +17,17 @@ import numpy as np
 
 __all__ = [
     "SylvError", "lib_path", "load", "SylvOpts", "SylvInfo", "SylvShift", "SylvCsr",
-    "STRATEGIES", "sylv_opts_default", "sylv_last_error", "sylv_op_create", "sylv_op_format",
-    "sylv_op_apply", "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval",
+    "STRATEGIES", "sylv_opts_default", "sylv_last_error", "sylv_op_create", "sylv_op_create_g",
+    "sylv_adi_create_g", "sylv_op_format",
+    "sylv_op_apply", "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_bicgstab", "sylv_arnoldi",
+    "sylv_controller_eval",
     "sylv_adi_create", "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve",
     "sylv_adi_info", "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "SylvesterADI",
-    "sylv_adi_profile", "sylv_adi_kernel_stats", "HIST_COLUMNS", "EXPORTED", "KERNELS",
+    "sylv_adi_profile", "sylv_adi_kernel_stats", "sylv_adi_core", "sylv_bicgstab", "sylv_arnoldi",
+    "HIST_COLUMNS", "EXPORTED", "KERNELS",
     "SylvProblem", "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info",
     "sylv_adi_batch_history", "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy",
-    "SylvesterADIBatch",
+    "SylvesterADIBatch", "sylv_adi_batch_set_rhs", "sylv_adi_batch_profile", "sylv_adi_batch_kernel_stats",
 ]
 
 SYLV_OK = 0
@@ -34,16 +37,19 @@ WARNINGS = (-4, -5)      # solve finished, factors valid
 STRATEGIES = {"fixed": 0, "nobl_mid": 1, "bl_mid": 2, "nobl_A": 3, "bl_A": 4, "nobl_B": 5, "bl_B": 6}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 ORTHO = {"cgs2": 0, "dcgs2": 1}
+INNER = {"gmres": 0, "bicgstab": 1}
 HIST_COLUMNS = ("k", "alpha", "beta", "dA", "dB", "eps_hat", "nrA", "nrB", "itsA", "itsB",
                 "u", "v", "res_comp", "N_w")
 EXPORTED = (
-    "sylv_last_error", "sylv_opts_default", "sylv_op_create", "sylv_op_format", "sylv_op_apply",
-    "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_controller_eval", "sylv_adi_create",
-    "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
-    "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "sylv_adi_profile",
+    "sylv_last_error", "sylv_opts_default", "sylv_op_create", "sylv_op_create_g", "sylv_op_format",
+    "sylv_op_apply", "sylv_op_destroy", "sylv_cgs2", "sylv_gmres", "sylv_bicgstab", "sylv_arnoldi",
+    "sylv_controller_eval", "sylv_adi_create",
+    "sylv_adi_create_g", "sylv_adi_set_rhs", "sylv_adi_set_rhs_device", "sylv_adi_solve", "sylv_adi_info",
+    "sylv_adi_history", "sylv_adi_factors", "sylv_adi_destroy", "sylv_adi_core", "sylv_adi_profile",
     "sylv_adi_kernel_stats", "sylv_cgs2_noalloc", "sylv_cgs2_noalloc_max_rows",
     "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info", "sylv_adi_batch_history",
-    "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy",
+    "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy", "sylv_adi_batch_set_rhs",
+    "sylv_adi_batch_profile", "sylv_adi_batch_kernel_stats",
 )
 KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3", "restart_update", "restart_residual",
            "adi_controller", "adi_step_init", "adi_gram")
@@ -71,7 +77,8 @@ class SylvOpts(C.Structure):
                 ("strategy", C.c_int32), ("fixed_tol", C.c_double), ("restart", C.c_int32),
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
                 ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32),
-                ("ortho", C.c_int32), ("restart_every", C.c_int32)]
+                ("ortho", C.c_int32), ("restart_every", C.c_int32), ("inner", C.c_int32),
+                ("real_pairs", C.c_int32)]
 
 
 class SylvProblem(C.Structure):
@@ -114,15 +121,21 @@ def load():
         "sylv_last_error": ([], C.c_char_p),
         "sylv_opts_default": ([C.POINTER(SylvOpts)], C.c_int),
         "sylv_op_create": ([C.POINTER(SylvCsr), i32, C.POINTER(vp)], C.c_int),
+        "sylv_op_create_g": ([C.POINTER(SylvCsr), C.POINTER(SylvCsr), i32, C.POINTER(vp)], C.c_int),
         "sylv_op_format": ([vp, pi32, pi32, pi32], C.c_int),
         "sylv_op_apply": ([vp, SylvShift, i32, i32, vp, vp, i32, vp], C.c_int),
         "sylv_op_destroy": ([vp], C.c_int),
         "sylv_cgs2": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
         "sylv_gmres": ([vp, SylvShift, i32, i32, vp, vp, i32, d, i32, i32, i32, pi32, pd, pd, vp], C.c_int),
+        "sylv_bicgstab": ([vp, SylvShift, i32, i32, vp, vp, i32, d, i32, i32, pi32, pd, pd, vp], C.c_int),
+        "sylv_arnoldi": ([vp, SylvShift, i32, i32, vp, i32, i32, i32, vp, vp, vp], C.c_int),
         "sylv_controller_eval": ([C.POINTER(SylvOpts), i32, pd, pd], C.c_int),
         "sylv_adi_create": ([C.POINTER(SylvCsr), C.POINTER(SylvCsr), pd, pd, i32,
                              C.POINTER(SylvShift), C.POINTER(SylvShift), i32, d,
                              C.POINTER(SylvOpts), vp, C.POINTER(vp)], C.c_int),
+        "sylv_adi_create_g": ([C.POINTER(SylvCsr), C.POINTER(SylvCsr), C.POINTER(SylvCsr),
+                               C.POINTER(SylvCsr), pd, pd, i32, C.POINTER(SylvShift), C.POINTER(SylvShift),
+                               i32, d, C.POINTER(SylvOpts), vp, C.POINTER(vp)], C.c_int),
         "sylv_adi_set_rhs": ([vp, pd, pd], C.c_int),
         "sylv_adi_set_rhs_device": ([vp, vp, vp], C.c_int),
         "sylv_adi_solve": ([vp], C.c_int),
@@ -130,6 +143,7 @@ def load():
         "sylv_adi_history": ([vp, pd, i32, pi32], C.c_int),
         "sylv_adi_factors": ([vp, vp, vp, vp, i32, pi32, pi32], C.c_int),
         "sylv_adi_destroy": ([vp], C.c_int),
+        "sylv_adi_core": ([vp, pd, i32, pi32], C.c_int),
         "sylv_adi_profile": ([vp, i32], C.c_int),
         "sylv_adi_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "sylv_cgs2_noalloc": ([vp, i32, i32, vp, pd, vp], C.c_int),
@@ -141,6 +155,9 @@ def load():
         "sylv_adi_batch_factors": ([vp, i32, vp, vp, vp, i32, pi32, pi32], C.c_int),
         "sylv_adi_batch_stats": ([vp, C.POINTER(C.c_int64), pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "sylv_adi_batch_destroy": ([vp], C.c_int),
+        "sylv_adi_batch_set_rhs": ([vp, i32, pd, pd], C.c_int),
+        "sylv_adi_batch_profile": ([vp, i32], C.c_int),
+        "sylv_adi_batch_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -196,6 +213,8 @@ def sylv_opts_default(**overrides) -> SylvOpts:
             v = PRECISIONS[v]
         if k == "ortho" and isinstance(v, str):
             v = ORTHO[v]
+        if k == "inner" and isinstance(v, str):
+            v = INNER[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
@@ -219,11 +238,20 @@ def _csr(M) -> _HostCsr:
     return _HostCsr(M.shape[0], M.indptr, M.indices, M.data)   # scipy.sparse.csr_matrix
 
 
-def sylv_op_create(M, transpose: bool = False) -> int:
+def sylv_op_create(M, transpose: bool = False, mass=None) -> int:
+    """Device operator Op (or Op + sigma Mass with a mass matrix, for the
+    generalized equation)."""
     h = _csr(M)
     out = C.c_void_p()
-    _check(load().sylv_op_create(C.byref(h.s), int(transpose), C.byref(out)))
+    if mass is None:
+        _check(load().sylv_op_create(C.byref(h.s), int(transpose), C.byref(out)))
+    else:
+        hm = _csr(mass)
+        _check(load().sylv_op_create_g(C.byref(h.s), C.byref(hm.s), int(transpose), C.byref(out)))
     return out.value
+
+
+sylv_op_create_g = sylv_op_create
 
 
 def sylv_op_format(op) -> tuple[int, int, int]:
@@ -253,7 +281,17 @@ def sylv_cgs2_noalloc(V, n, k, w, stream=None) -> np.ndarray:
     """CGS2 step that allocates no GPU memory (static scratch in the library).
 
     V: device n x (k+1) float64, column-major; column k receives the
-    normalised result.  w: device n float64 (read only).  Returns h (k+1)."""
+    normalised result.  w: device n float64 (read only).  Returns h (k+1).
+    Torch tensors are checked (CUDA, float64, contiguous, large enough)
+    before the library writes into them; integer addresses are passed on as
+    they are."""
+    n, k = int(n), int(k)
+    for name, x, need in (("V", V, n * (k + 1)), ("w", w, n)):
+        if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+            if not x.is_cuda or str(x.dtype) != "torch.float64" or not x.is_contiguous():
+                raise SylvError(-1, f"sylv_cgs2_noalloc: {name} must be a contiguous float64 CUDA tensor")
+            if x.numel() < need:
+                raise SylvError(-1, f"sylv_cgs2_noalloc: {name} holds {x.numel()} values, needs {need}")
     h = np.zeros(k + 1)
     _check(load().sylv_cgs2_noalloc(_ptr(V), int(n), int(k), _ptr(w),
                                     h.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
@@ -281,6 +319,32 @@ def sylv_gmres(op, sigma, jacobi, is_complex, B, X, ncols, tol, restart, max_ite
     return rc, iters, res, hist
 
 
+def sylv_bicgstab(op, sigma, jacobi, is_complex, B, X, ncols, tol, max_iters,
+                  want_hist=False, stream=None, precision="fp64"):
+    """BiCGstab for ncols columns; returns (status, iters[ncols], resnorm[ncols], hist or None)."""
+    iters = np.zeros(ncols, dtype=np.int32)
+    res = np.zeros(ncols)
+    hist = np.zeros((ncols, max_iters)) if want_hist else None
+    rc = load().sylv_bicgstab(op, _shift(sigma), int(jacobi), int(is_complex), _ptr(B), _ptr(X),
+                              int(ncols), float(tol), int(max_iters), PRECISIONS.get(precision, precision),
+                              iters.ctypes.data_as(C.POINTER(C.c_int32)),
+                              res.ctypes.data_as(C.POINTER(C.c_double)),
+                              hist.ctypes.data_as(C.POINTER(C.c_double)) if want_hist else None,
+                              _stream(stream))
+    _check(rc, allow_warn=True)
+    return rc, iters, res, hist
+
+
+def sylv_arnoldi(op, sigma, jacobi, is_complex, v0, k, V_out, precision="fp64", ortho="cgs2", stream=None):
+    """One Arnoldi cycle of k steps; V_out (device, n x (k+1)) receives the
+    basis; returns the (k+1) x k Hessenberg matrix as formed."""
+    H = np.zeros((k, k + 1), dtype=np.complex128 if is_complex else np.float64)   # column-major (k+1) x k
+    _check(load().sylv_arnoldi(op, _shift(sigma), int(jacobi), int(is_complex), _ptr(v0), int(k),
+                               PRECISIONS.get(precision, precision), ORTHO.get(ortho, ortho), _ptr(V_out),
+                               H.ctypes.data, _stream(stream)))
+    return H.T.copy()
+
+
 def sylv_controller_eval(opts: SylvOpts, inputs: np.ndarray) -> np.ndarray:
     inp = np.ascontiguousarray(inputs, dtype=np.float64).reshape(-1, 11)
     out = np.zeros((inp.shape[0], 3))
@@ -290,8 +354,13 @@ def sylv_controller_eval(opts: SylvOpts, inputs: np.ndarray) -> np.ndarray:
     return out
 
 
-def sylv_adi_create(A, B, f, g, alpha, beta, tau, opts: SylvOpts | None = None, stream=None) -> int:
+def sylv_adi_create(A, B, f, g, alpha, beta, tau, opts: SylvOpts | None = None, stream=None,
+                    M=None, Cm=None) -> int:
+    """Solver handle for A X + X B = -f g^*, or with mass matrices M, Cm for the
+    generalized A X Cm + M X B = -f g^* (sylv_adi_create_g)."""
     ha, hb = _csr(A), _csr(B)
+    hm = _csr(M) if M is not None else None
+    hc = _csr(Cm) if Cm is not None else None
     f = np.asfortranarray(f, dtype=np.float64)
     g = np.asfortranarray(g, dtype=np.float64)
     r = f.shape[1]
@@ -302,11 +371,20 @@ def sylv_adi_create(A, B, f, g, alpha, beta, tau, opts: SylvOpts | None = None, 
     if len(alpha) != len(beta):
         raise ValueError("alpha and beta need the same length")
     out = C.c_void_p()
-    _check(load().sylv_adi_create(C.byref(ha.s), C.byref(hb.s),
-                                  f.ctypes.data_as(C.POINTER(C.c_double)),
-                                  g.ctypes.data_as(C.POINTER(C.c_double)), r, al, be, len(alpha),
-                                  float(tau), C.byref(opts) if opts is not None else None,
-                                  _stream(stream), C.byref(out)))
+    if hm is None and hc is None:
+        _check(load().sylv_adi_create(C.byref(ha.s), C.byref(hb.s),
+                                      f.ctypes.data_as(C.POINTER(C.c_double)),
+                                      g.ctypes.data_as(C.POINTER(C.c_double)), r, al, be, len(alpha),
+                                      float(tau), C.byref(opts) if opts is not None else None,
+                                      _stream(stream), C.byref(out)))
+    else:
+        _check(load().sylv_adi_create_g(C.byref(ha.s), C.byref(hb.s),
+                                        C.byref(hm.s) if hm is not None else None,
+                                        C.byref(hc.s) if hc is not None else None,
+                                        f.ctypes.data_as(C.POINTER(C.c_double)),
+                                        g.ctypes.data_as(C.POINTER(C.c_double)), r, al, be, len(alpha),
+                                        float(tau), C.byref(opts) if opts is not None else None,
+                                        _stream(stream), C.byref(out)))
     return out.value
 
 
@@ -339,10 +417,26 @@ def sylv_adi_history(h, cap: int = 1000) -> np.ndarray:
     return buf[: rows.value]
 
 
-def sylv_adi_factors(h, n: int, m: int):
-    """(Z, Y, gamma) as numpy arrays (host copies)."""
+def sylv_adi_core(h) -> np.ndarray:
+    """The real kr x kr core G of X = Z G Y^T (real factors only)."""
+    kr = C.c_int32()
+    _check(load().sylv_adi_core(h, None, 0, C.byref(kr)))
+    G = np.zeros((kr.value, kr.value))                    # column-major == transposed row-major
+    _check(load().sylv_adi_core(h, G.ctypes.data_as(C.POINTER(C.c_double)), max(1, kr.value), C.byref(kr)))
+    return G.T.copy()
+
+
+def sylv_adi_factors(h, n: int, m: int, real_pairs: bool = False):
+    """(Z, Y, gamma) as numpy arrays (host copies).  With real double steps
+    (real_pairs) the third item is the dense real core G (X = Z G Y^T)."""
     info = sylv_adi_info(h)
     kr, cplx = info["kr"], info["is_complex"]
+    if real_pairs:
+        Z = np.zeros((kr, n))
+        Y = np.zeros((kr, m))
+        kro, isc = C.c_int32(), C.c_int32()
+        _check(load().sylv_adi_factors(h, Z.ctypes.data, Y.ctypes.data, None, 0, C.byref(kro), C.byref(isc)))
+        return Z.T, Y.T, sylv_adi_core(h)
     dt = np.complex128 if cplx else np.float64
     Z = np.zeros((kr, n), dtype=dt)        # column-major n x kr == row-major kr x n
     Y = np.zeros((kr, m), dtype=dt)
@@ -377,12 +471,13 @@ def sylv_adi_kernel_stats(h) -> dict:
 class SylvesterADI:
     """A X + X B = -f g^* solved on the GPU by the inexact LR-ADI iteration."""
 
-    def __init__(self, A, B, f, g, alpha, beta, tau=1e-8, stream=None, **opts):
+    def __init__(self, A, B, f, g, alpha, beta, tau=1e-8, stream=None, M=None, Cm=None, **opts):
+        """M, Cm: mass matrices of the generalized equation A X Cm + M X B = -f g^*."""
         self.n = A.n if hasattr(A, "n") else A.shape[0]
         self.m = B.n if hasattr(B, "n") else B.shape[0]
         self.r = f.shape[1]
         self.opts = sylv_opts_default(**opts)
-        self.h = sylv_adi_create(A, B, f, g, alpha, beta, tau, self.opts, stream)
+        self.h = sylv_adi_create(A, B, f, g, alpha, beta, tau, self.opts, stream, M=M, Cm=Cm)
 
     def solve(self) -> int:
         return sylv_adi_solve(self.h)
@@ -397,7 +492,9 @@ class SylvesterADI:
         return sylv_adi_history(self.h)
 
     def factors(self):
-        return sylv_adi_factors(self.h, self.n, self.m)
+        """(Z, Y, gamma); with real double steps (real_pairs=1) (Z, Y, G) with
+        the dense real core G, X = Z G Y^T."""
+        return sylv_adi_factors(self.h, self.n, self.m, bool(self.opts.real_pairs))
 
     def profile(self, enable: bool = True) -> None:
         sylv_adi_profile(self.h, enable)
@@ -490,6 +587,30 @@ def sylv_adi_batch_destroy(b) -> None:
     _check(load().sylv_adi_batch_destroy(b))
 
 
+def sylv_adi_batch_set_rhs(b, i: int, f, g) -> None:
+    f = np.asfortranarray(f, dtype=np.float64)
+    g = np.asfortranarray(g, dtype=np.float64)
+    _check(load().sylv_adi_batch_set_rhs(b, int(i), f.ctypes.data_as(C.POINTER(C.c_double)),
+                                         g.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def sylv_adi_batch_profile(b, enable: bool) -> None:
+    _check(load().sylv_adi_batch_profile(b, int(enable)))
+
+
+def sylv_adi_batch_kernel_stats(b) -> dict:
+    """{kernel: (ms, algorithmic bytes, algorithmic flops, launches)} of the batch since the last reset."""
+    ms = np.zeros(len(KERNELS))
+    by = np.zeros(len(KERNELS))
+    fl = np.zeros(len(KERNELS))
+    la = np.zeros(len(KERNELS), dtype=np.int64)
+    _check(load().sylv_adi_batch_kernel_stats(b, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                              by.ctypes.data_as(C.POINTER(C.c_double)),
+                                              fl.ctypes.data_as(C.POINTER(C.c_double)),
+                                              la.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {k: (float(ms[i]), float(by[i]), float(fl[i]), int(la[i])) for i, k in enumerate(KERNELS)}
+
+
 class SylvesterADIBatch:
     """Many independent A_i X + X B_i = -f_i g_i^* solved in one device loop.
 
@@ -521,6 +642,15 @@ class SylvesterADIBatch:
 
     def stats(self) -> dict:
         return sylv_adi_batch_stats(self.h)
+
+    def set_rhs(self, i: int, f, g) -> None:
+        sylv_adi_batch_set_rhs(self.h, i, f, g)
+
+    def profile(self, enable: bool = True) -> None:
+        sylv_adi_batch_profile(self.h, enable)
+
+    def kernel_stats(self) -> dict:
+        return sylv_adi_batch_kernel_stats(self.h)
 
     def close(self) -> None:
         if self.h:

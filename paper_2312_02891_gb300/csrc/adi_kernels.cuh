@@ -3,7 +3,7 @@
 // initialisation of the 2r column solves, and the fused factor update +
 // Gram kernel that evaluates the residual norm and the outer stop test.
 #pragma once
-#include "gmres_kernels.cuh"
+#include "bicg_kernels.cuh"
 
 namespace sylv {
 
@@ -70,6 +70,13 @@ struct AdiState {
     double dA, dB, eh;
     T alpha_k, beta_k, gamma_k;
     long long itsA, itsB, cycles;
+    // real double step of a conjugate pair (AdiDev::real_pairs): the step is a
+    // pair; the pair's shift on the A side (beta) / B side (alpha) is complex;
+    // the second (real-shift) solves are running; inner steps and stalled
+    // solves of the pair's first solves
+    int pair, cplxA, cplxB, stage2;
+    long long pitsA, pitsB;
+    int pstalled;
 };
 
 template <typename T, typename S, typename C>
@@ -98,6 +105,24 @@ struct AdiDev {
     int nchA, nchB, rpc;
     AdiState<T>* s;
     int* h_done;            // mapped host word
+    // real double step of conjugate pairs (Sec. 3.3 "Complex shift parameters"),
+    // complex instantiations only: the solves write XA, XB (n x r, m x r,
+    // complex); the second solves of a real-shift side write XA2, XB2; the real
+    // factors go to Zr, Yr (n x (kmax + 1) r, m x (kmax + 1) r); core holds per
+    // step {kind, G00, G01, G10, G11} (kind 1: plain step, G00 = gamma; 2: first
+    // step of a pair, G its 2 x 2 real core; 3: second step of a pair); RsA, RsB
+    // keep the first residual of a real-shift side (n x r, m x r)
+    int real_pairs;
+    T* XA;
+    T* XB;
+    T* XA2;
+    T* XB2;
+    double* Zr;
+    double* Yr;
+    double* core;
+    double* RsA;
+    double* RsB;
+    double* pgpart;         // (nchA + nchB) x SYLV_PGSTRIDE Gram partials of the pair update
 };
 
 // Largest eigenvalues of small Hermitian matrices (cyclic Jacobi, Golub and
@@ -202,6 +227,19 @@ __device__ void adi_begin_step(const AdiDev<T, S, C>& d) {
     s->beta_k = b;
     s->gamma_k = -(b + a);
     s->dA = dA; s->dB = dB; s->eh = eh;
+    // real double step: one solve per column and side for the pair, to a
+    // tolerance divided so that both steps of the pair meet delta / r:
+    // 1 + |gamma| / |Im(shift)| for a complex shift (the second solution is
+    // derived), 2 for a real shift (two real solves)
+    const bool pair = d.real_pairs && is_pair_start(d.alpha, d.beta, idx, d.nshift);
+    const double ag = absv(s->gamma_k);
+    s->pair = pair ? 1 : 0;
+    s->cplxA = im(b) != 0.0;
+    s->cplxB = im(a) != 0.0;
+    s->stage2 = 0;
+    s->pitsA = 0; s->pitsB = 0; s->pstalled = 0;
+    const double facA = !pair ? 1.0 : (s->cplxA ? 1.0 + ag / fabs(im(b)) : 2.0);
+    const double facB = !pair ? 1.0 : (s->cplxB ? 1.0 + ag / fabs(im(a)) : 2.0);
     for (int q = 0; q < 2 * r; ++q) {
         SysState<T>& st = d.st[q];
         const bool sideA = q < r;
@@ -211,14 +249,14 @@ __device__ void adi_begin_step(const AdiDev<T, S, C>& d) {
         st.max_iters = d.max_inner;
         st.resnorm = 0.0; st.est = 0.0;
         if (sideA) {
-            st.tol = dA / r;
+            st.tol = dA / r / facA;
             st.sigma = b;
-            st.x = d.Z + ((size_t)(k - 1) * r + l) * d.n;
+            st.x = d.real_pairs ? d.XA + (size_t)l * d.n : d.Z + ((size_t)(k - 1) * r + l) * d.n;
             st.b = d.w + (size_t)l * d.n;
         } else {
-            st.tol = dB / r;
+            st.tol = dB / r / facB;
             st.sigma = conjg(a);
-            st.x = d.Y + ((size_t)(k - 1) * r + l) * d.m;
+            st.x = d.real_pairs ? d.XB + (size_t)l * d.m : d.Y + ((size_t)(k - 1) * r + l) * d.m;
             st.b = d.t + (size_t)l * d.m;
         }
     }
@@ -262,7 +300,7 @@ __device__ __forceinline__ void adi_step_rows(const AdiDev<T, S, C>& d, int bi) 
     T* pinv = sideA ? d.pinvA : d.pinvB;
     C* aval = sideA ? d.avalA : d.avalB;
     const OpDesc& op = sideA ? d.opA : d.opB;
-    T* X = (sideA ? d.Z : d.Y) + (size_t)(s->k - 1) * d.r * nn;
+    T* X = d.real_pairs ? (sideA ? d.XA : d.XB) : (sideA ? d.Z : d.Y) + (size_t)(s->k - 1) * d.r * nn;
     count_work(d.ctl, K_STEP, chunk,
                (double)d.r * nn * sizeof(T) + (pinv ? (double)nn * (sizeof(T) + sizeof(double)) : 0.0) +
                (aval ? (double)op.ndiag * nn * (sizeof(double) + sizeof(C)) : 0.0),
@@ -328,13 +366,17 @@ __device__ bool adi_gram_body(const AdiDev<T, S, C>& d, int init, int bi) {
         const T gm = sideA ? s->gamma_k : conjg(s->gamma_k);
         const T* X = (sideA ? d.Z : d.Y) + (size_t)(s->k - 1) * r * nn;
         const SysDesc<T, S, C>* sd = d.sd + (sideA ? 0 : r);
+        // generalized equation: w_k = w_{k-1} + gamma M z_k, t_k = t_{k-1} +
+        // conj(gamma) C^* y_k (eq. (lradi_g)); u, v use ||M z||, ||C^T y||
+        const OpDesc& op = sideA ? d.opA : d.opB;
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             T wv[SYLV_MAXR], zv[SYLV_MAXR], rv[SYLV_MAXR];
 #pragma unroll
             for (int l = 0; l < SYLV_MAXR; ++l) {
                 if (l < r) {
-                    zv[l] = X[(size_t)l * nn + i];
-                    rv[l] = cvt<T>(sd[l].V[BasisIx<1>::row(sd[l], i)]);
+                    const T* xl = X + (size_t)l * nn;
+                    zv[l] = mass_row<T>(op, i, [&](int q) { return xl[q]; });
+                    rv[l] = sd[l].rres ? cvt<T>(sd[l].rres[i]) : cvt<T>(sd[l].V[BasisIx<1>::row(sd[l], i)]);
                     wv[l] = W[(size_t)l * nn + i] + gm * zv[l];
                     W[(size_t)l * nn + i] = wv[l];
                 }

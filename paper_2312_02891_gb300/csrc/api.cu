@@ -78,6 +78,18 @@ static int resolve_opts(const sylv_opts* opts, double tol, sylv_opts* o) {
         set_error("precision %d not built", o->precision);
         return SYLV_ERR_UNSUPPORTED;
     }
+    if (o->inner != SYLV_INNER_GMRES && o->inner != SYLV_INNER_BICGSTAB) {
+        set_error("unknown inner solver %d", o->inner);
+        return SYLV_ERR_INVALID;
+    }
+    if (o->real_pairs != 0 && o->real_pairs != 1) {
+        set_error("real_pairs must be 0 or 1");
+        return SYLV_ERR_INVALID;
+    }
+    if (o->inner == SYLV_INNER_BICGSTAB && o->precision == SYLV_PREC_BF16) {
+        set_error("BiCGstab keeps no Krylov basis: use SYLV_PREC_FP32 (float32 vectors) or SYLV_PREC_FP64");
+        return SYLV_ERR_UNSUPPORTED;
+    }
     return SYLV_OK;
 }
 
@@ -103,22 +115,34 @@ int sylv_opts_default(sylv_opts* o) {
     o->driver = 1;
     o->ortho = SYLV_ORTHO_CGS2;
     o->restart_every = 4;
+    o->inner = SYLV_INNER_GMRES;
+    o->real_pairs = 0;
+    return SYLV_OK;
+}
+
+int sylv_op_create_g(const sylv_csr* csr, const sylv_csr* mass, int32_t transpose, sylv_op** out) {
+    if (!out) { set_error("sylv_op_create: null out"); return SYLV_ERR_INVALID; }
+    *out = nullptr;
+    HostCsr h, ht, hm, hmt;
+    SYLV_TRY(load_csr(csr, h));
+    if (mass) SYLV_TRY(load_csr(mass, hm));
+    sylv_op* op = new (std::nothrow) sylv_op();
+    if (!op) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
+    int rc;
+    if (transpose) {
+        transpose_csr(h, ht);
+        if (mass) transpose_csr(hm, hmt);
+        rc = op->op.upload(ht, mass ? &hmt : nullptr);
+    } else {
+        rc = op->op.upload(h, mass ? &hm : nullptr);
+    }
+    if (rc != SYLV_OK) { op->op.release(); delete op; return rc; }
+    *out = op;
     return SYLV_OK;
 }
 
 int sylv_op_create(const sylv_csr* csr, int32_t transpose, sylv_op** out) {
-    if (!out) { set_error("sylv_op_create: null out"); return SYLV_ERR_INVALID; }
-    *out = nullptr;
-    HostCsr h, ht;
-    SYLV_TRY(load_csr(csr, h));
-    sylv_op* op = new (std::nothrow) sylv_op();
-    if (!op) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
-    int rc;
-    if (transpose) { transpose_csr(h, ht); rc = op->op.upload(ht); }
-    else rc = op->op.upload(h);
-    if (rc != SYLV_OK) { op->op.release(); delete op; return rc; }
-    *out = op;
-    return SYLV_OK;
+    return sylv_op_create_g(csr, nullptr, transpose, out);
 }
 
 int sylv_op_format(const sylv_op* op, int32_t* is_stencil, int32_t* ndiag, int32_t* n) {
@@ -164,13 +188,42 @@ int sylv_gmres(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_c
     return fn(op->op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters_out, resnorm_out, hist_out, s);
 }
 
+int sylv_arnoldi(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex, const void* v0,
+                 int32_t k, int32_t precision, int32_t ortho, void* V_out, void* H_out, void* stream) {
+    if (!op) { set_error("sylv_arnoldi: null op"); return SYLV_ERR_INVALID; }
+    if (!is_complex && shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
+    if (precision < SYLV_PREC_FP64 || precision > SYLV_PREC_BF16) { set_error("unknown precision %d", precision); return SYLV_ERR_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto fn = is_complex ? (precision == SYLV_PREC_FP32 ? arnoldi_c64 : precision == SYLV_PREC_BF16 ? arnoldi_cbf : arnoldi_c128)
+                         : (precision == SYLV_PREC_FP32 ? arnoldi_r32 : precision == SYLV_PREC_BF16 ? arnoldi_rbf : arnoldi_r64);
+    return fn(op->op, sigma, jacobi, v0, k, ortho, V_out, H_out, s);
+}
+
+int sylv_bicgstab(const sylv_op* op, sylv_shift sigma, int32_t jacobi, int32_t is_complex,
+                  const void* B, void* X, int32_t ncols, double tol, int32_t max_iters,
+                  int32_t precision, int32_t* iters_out, double* resnorm_out, double* hist_out,
+                  void* stream) {
+    if (!op) { set_error("sylv_bicgstab: null op"); return SYLV_ERR_INVALID; }
+    if (!(tol >= 0.0)) { set_error("sylv_bicgstab: tol must be >= 0"); return SYLV_ERR_INVALID; }
+    if (!is_complex && shift_is_complex(sigma)) { set_error("complex shift with real vectors"); return SYLV_ERR_INVALID; }
+    if (precision != SYLV_PREC_FP64 && precision != SYLV_PREC_FP32) {
+        set_error("sylv_bicgstab: precision %d not built (FP64 or FP32)", precision);
+        return precision == SYLV_PREC_BF16 ? SYLV_ERR_UNSUPPORTED : SYLV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto fn = is_complex ? (precision == SYLV_PREC_FP32 ? bicgstab_c64 : bicgstab_c128)
+                         : (precision == SYLV_PREC_FP32 ? bicgstab_r32 : bicgstab_r64);
+    return fn(op->op, sigma, jacobi, B, X, ncols, tol, max_iters, iters_out, resnorm_out, hist_out, s);
+}
+
 int sylv_controller_eval(const sylv_opts* o, int32_t count, const double* in, double* out) {
     return controller_eval_dev(o, count, in, out);
 }
 
-int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const double* g,
-                    int32_t r, const sylv_shift* alpha, const sylv_shift* beta, int32_t n_shifts,
-                    double tol, const sylv_opts* opts, void* stream, sylv_handle** out) {
+int sylv_adi_create_g(const sylv_csr* A, const sylv_csr* B, const sylv_csr* M, const sylv_csr* Cm,
+                      const double* f, const double* g, int32_t r, const sylv_shift* alpha,
+                      const sylv_shift* beta, int32_t n_shifts, double tol, const sylv_opts* opts,
+                      void* stream, sylv_handle** out) {
     if (!out) { set_error("sylv_adi_create: null out"); return SYLV_ERR_INVALID; }
     *out = nullptr;
     sylv_opts o;
@@ -178,15 +231,29 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
     int vrc = check_problem(f, g, r, alpha, beta, n_shifts, tol, &cplx);
     if (vrc == SYLV_OK) vrc = resolve_opts(opts, tol, &o);
     if (vrc != SYLV_OK) return vrc;
+    if ((M || Cm) && cplx && o.real_pairs) {
+        set_error("the real double step is not built for the generalized equation (real_pairs = 0)");
+        return SYLV_ERR_UNSUPPORTED;
+    }
     sylv_handle* h = new (std::nothrow) sylv_handle();
     if (!h) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
     h->stream = (cudaStream_t)stream;
-    h->is_complex = cplx ? 1 : 0;
-    HostCsr ha, hb, hbt;
+    h->is_complex = (cplx && !o.real_pairs) ? 1 : 0;      // real double steps give real factors
+    HostCsr ha, hb, hbt, hm, hc, hct;
     int rc = load_csr(A, ha);
     if (rc == SYLV_OK) rc = load_csr(B, hb);
-    if (rc == SYLV_OK) { transpose_csr(hb, hbt); rc = h->A.upload(ha); }
-    if (rc == SYLV_OK) rc = h->Bt.upload(hbt);
+    if (rc == SYLV_OK && M) rc = load_csr(M, hm);
+    if (rc == SYLV_OK && Cm) rc = load_csr(Cm, hc);
+    if (rc == SYLV_OK && ((M && hm.n != ha.n) || (Cm && hc.n != hb.n))) {
+        set_error("M must match A and C must match B in size");
+        rc = SYLV_ERR_INVALID;
+    }
+    // the B-side systems use (B + alpha C)^* = B^T + conj(alpha) C^T (real B, C)
+    if (rc == SYLV_OK) { transpose_csr(hb, hbt); rc = h->A.upload(ha, M ? &hm : nullptr); }
+    if (rc == SYLV_OK) {
+        if (Cm) transpose_csr(hc, hct);
+        rc = h->Bt.upload(hbt, Cm ? &hct : nullptr);
+    }
     if (rc == SYLV_OK) {
         AdiArgs a{&h->A, &h->Bt, ha.n, hb.n, r, f, g, alpha, beta, n_shifts, tol, o, h->stream};
         auto mk = cplx ? (o.precision == SYLV_PREC_FP32 ? make_adi_c64 : o.precision == SYLV_PREC_BF16 ? make_adi_cbf : make_adi_c128)
@@ -201,6 +268,12 @@ int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const
     }
     *out = h;
     return SYLV_OK;
+}
+
+int sylv_adi_create(const sylv_csr* A, const sylv_csr* B, const double* f, const double* g,
+                    int32_t r, const sylv_shift* alpha, const sylv_shift* beta, int32_t n_shifts,
+                    double tol, const sylv_opts* opts, void* stream, sylv_handle** out) {
+    return sylv_adi_create_g(A, B, nullptr, nullptr, f, g, r, alpha, beta, n_shifts, tol, opts, stream, out);
 }
 
 int sylv_adi_set_rhs(sylv_handle* h, const double* f, const double* g) {
@@ -237,6 +310,15 @@ int sylv_adi_factors(const sylv_handle* h, void* Z, void* Y, void* gamma, int32_
     if (!h->solved) { set_error("no solve yet"); return SYLV_ERR_NOT_SOLVED; }
     if (is_complex) *is_complex = h->is_complex;
     return h->impl->factors(Z, Y, gamma, on_device, kr_out);
+}
+
+int sylv_adi_core(const sylv_handle* h, double* G, int32_t ld, int32_t* kr_out) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    if (!h->solved) { set_error("no solve yet"); return SYLV_ERR_NOT_SOLVED; }
+    int kr = 0;
+    const int rc = h->impl->core(G, ld, &kr);
+    if (kr_out) *kr_out = kr;
+    return rc;
 }
 
 int sylv_adi_profile(sylv_handle* h, int32_t enable) {
@@ -288,6 +370,10 @@ int sylv_adi_batch_create(int32_t count, const sylv_problem* probs, const sylv_o
         cplx |= ci;
     }
     o = per[0];
+    if (cplx && o.real_pairs) {
+        set_error("batch: the real double step of conjugate pairs is not built for batches (real_pairs = 0)");
+        return SYLV_ERR_UNSUPPORTED;
+    }
     sylv_batch* b = new (std::nothrow) sylv_batch();
     if (!b) { set_error("host allocation failed"); return SYLV_ERR_NOMEM; }
     b->count = count;
@@ -357,6 +443,21 @@ int sylv_adi_batch_factors(const sylv_batch* b, int32_t i, void* Z, void* Y, voi
 int sylv_adi_batch_stats(const sylv_batch* b, int64_t* launches, double* bytes, double* flops, int64_t* ticks) {
     if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
     return b->impl->stats((long long*)launches, bytes, flops, (long long*)ticks);
+}
+
+int sylv_adi_batch_set_rhs(sylv_batch* b, int32_t i, const double* f, const double* g) {
+    SYLV_TRY(batch_index(b, i));
+    return b->impl->set_rhs(i, f, g);
+}
+
+int sylv_adi_batch_profile(sylv_batch* b, int32_t enable) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    return b->impl->profile(enable ? 1 : 0);
+}
+
+int sylv_adi_batch_kernel_stats(const sylv_batch* b, double* ms, double* bytes, double* flops, int64_t* launches) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    return b->impl->kernel_stats(ms, bytes, flops, (long long*)launches);
 }
 
 int sylv_adi_batch_destroy(sylv_batch* b) {

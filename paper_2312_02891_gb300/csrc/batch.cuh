@@ -50,7 +50,10 @@ k_batch_outer(const AdiDev<T, S, C>* __restrict__ ds, const BItem* __restrict__ 
     if (!adi_gram_body(d, init, it.bi)) return;
     if (s->done) {
         s->stage = BST_DONE;
-        atomicSub(&ctl->n_inst_open, 1);
+        if (atomicSub(&ctl->n_inst_open, 1) == 1 && ctl->h_open) {
+            *(volatile int*)ctl->h_open = 0;
+            __threadfence_system();
+        }
     } else {
         adi_begin_step(d);
         atomicAdd(&ctl->n_active, 2 * d.r);
@@ -105,9 +108,128 @@ struct Batch : BatchBase {
     std::vector<int> inst_status;
     long long launches_last = 0;
 
+    int driver = 0;                 // 0: one CUDA graph per solve; 1: host-driven device iterations
+    int restart_every = 1;
+    int* h_open = nullptr;          // mapped host word (host-driven solves)
+    int* d_hopen = nullptr;
+    cudaEvent_t bev[4][3] = {};     // events around the outer kernels of sampled iterations
+    int bpend[4] = {0, 0, 0, 0};
+
     ~Batch() override {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
+        if (h_open) cudaFreeHost(h_open);
+        for (auto& row : bev)
+            for (auto& e : row)
+                if (e) cudaEventDestroy(e);
+    }
+
+    int profile(int on) override {
+        SYLV_TRY(eng.set_profile(on));
+        for (int sl = 0; sl < 4; ++sl) bpend[sl] = 0;
+        if (on && !bev[0][0])
+            for (auto& row : bev)
+                for (auto& e : row) SYLV_CK(cudaEventCreate(&e));
+        return SYLV_OK;
+    }
+
+    int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const override {
+        double b[K_COUNT], f[K_COUNT];
+        SYLV_TRY(eng.read_work(b, f));
+        for (int q = 0; q < K_COUNT; ++q) {
+            if (ms) ms[q] = eng.samples[q] > 0 ? eng.kernel_ms[q] / eng.samples[q] * eng.launches[q] : 0.0;
+            if (bytes) bytes[q] = b[q];
+            if (flops) flops[q] = f[q];
+            if (launches) launches[q] = eng.launches[q];
+        }
+        return SYLV_OK;
+    }
+
+    int harvest_outer(int slot) {
+        if (!bpend[slot]) return SYLV_OK;
+        SYLV_CK(cudaEventSynchronize(bev[slot][2]));
+        float m0 = 0.f, m1 = 0.f;
+        SYLV_CK(cudaEventElapsedTime(&m0, bev[slot][0], bev[slot][1]));
+        SYLV_CK(cudaEventElapsedTime(&m1, bev[slot][1], bev[slot][2]));
+        eng.kernel_ms[K_GRAM] += m0; eng.samples[K_GRAM] += 1;
+        eng.kernel_ms[K_STEP] += m1; eng.samples[K_STEP] += 1;
+        bpend[slot] = 0;
+        return SYLV_OK;
+    }
+
+    // Host-driven solve: the host launches every device iteration (outer
+    // kernel, step set-up, inner sweeps, restart kernels every restart_every
+    // iterations) until the device clears *h_open (every instance finished),
+    // with at most about eight iterations in flight; with profiling, the
+    // kernels of every fourth iteration are bracketed by CUDA events.
+    int solve_host() {
+        SYLV_CK(cudaMemsetAsync(st.p, 0, (size_t)count * sizeof(AdiState<T>), stream));
+        BatchCtl c{};
+        SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        unsigned long long l0 = 0;
+        for (int q = 0; q < K_COUNT; ++q) l0 += c.launch_count[q];
+        c.n_active = 0; c.ticks = 0; c.capped = 0; c.n_inst_open = count; c.graph = 0;
+        c.h_flag = nullptr;           // the inner-solve flag is not the end of a batch
+        c.h_open = d_hopen;
+        for (int q = 0; q < K_COUNT; ++q) c.gdone[q] = 0;
+        SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, stream));
+        SYLV_CK(cudaStreamSynchronize(stream));
+        *h_open = 1;
+        const long long max_ticks = (long long)(kmax + 2) * (max_inner + 8);
+        const int D = 4, G = eng.pdl ? 4 : 1, DE = eng.pdl ? 2 : D;
+        long long t = 0, grp = 0;
+        int rc = SYLV_OK;
+        while (*(volatile int*)h_open != 0) {
+            if (t >= max_ticks) {
+                set_error("batch: instances did not finish within %lld device iterations", max_ticks);
+                rc = SYLV_ERR_INNER_STALL;
+                break;
+            }
+            const int slot = (int)(t % D);
+            if (eng.pending[slot]) SYLV_TRY(eng.harvest(slot));
+            SYLV_TRY(harvest_outer(slot));
+            const bool sampled = eng.profile && (eng.tick_no % eng.prof_every) == 0;
+            if (sampled) SYLV_CK(cudaEventRecord(bev[slot][0], stream));
+            k_batch_outer<T, S, C><<<nbitems, SYLV_BLOCK, 0, stream>>>(d_ds.p, d_items.p, eng.d_ctl.p);
+            if (sampled) SYLV_CK(cudaEventRecord(bev[slot][1], stream));
+            k_batch_step<T, S, C><<<nbitems, SYLV_BLOCK, 0, stream>>>(d_ds.p, d_items.p, eng.d_ctl.p);
+            if (sampled) {
+                SYLV_CK(cudaEventRecord(bev[slot][2], stream));
+                bpend[slot] = 1;
+            }
+            SYLV_CK(cudaGetLastError());
+            eng.launches[K_GRAM]++; eng.launches[K_STEP]++;
+            SYLV_TRY(eng.launch_tick(0, slot, restart_every <= 1 || t % restart_every == 0));
+            ++t;
+            if (t % G == 0) {
+                SYLV_CK(cudaEventRecord(eng.ev[grp % DE], stream));
+                ++grp;
+                if (grp >= DE) SYLV_CK(cudaEventSynchronize(eng.ev[grp % DE]));
+            }
+        }
+        SYLV_CK(cudaStreamSynchronize(stream));
+        for (int sl = 0; sl < D; ++sl) {
+            if (eng.pending[sl]) SYLV_TRY(eng.harvest(sl));
+            SYLV_TRY(harvest_outer(sl));
+        }
+        eng.ticks += t;
+        SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        unsigned long long l1 = 0;
+        for (int q = 0; q < K_COUNT; ++q) l1 += c.launch_count[q];
+        launches_last = (long long)(l1 - l0);
+        ticks_last = t;
+        const int frc = finish();
+        return rc != SYLV_OK ? rc : frc;
+    }
+
+    int set_rhs(int i, const double* hf, const double* hg) override {
+        if (!hf || !hg) { set_error("batch set_rhs: null f or g"); return SYLV_ERR_INVALID; }
+        SYLV_CK(cudaMemcpyAsync((void*)hd[i].f, hf, (size_t)inst_n[i] * inst_r[i] * sizeof(double),
+                                cudaMemcpyHostToDevice, stream));
+        SYLV_CK(cudaMemcpyAsync((void*)hd[i].g, hg, (size_t)inst_m[i] * inst_r[i] * sizeof(double),
+                                cudaMemcpyHostToDevice, stream));
+        SYLV_CK(cudaStreamSynchronize(stream));
+        return SYLV_OK;
     }
 
     int init(const std::vector<BatchProb>& ps, const sylv_opts& o, cudaStream_t s) {
@@ -115,10 +237,15 @@ struct Batch : BatchBase {
         count = (int)ps.size();
         kmax = o.kmax;
         max_inner = o.max_inner;
-        std::vector<long long> rows;
-        for (const auto& p : ps)
+        std::vector<long long> rows, grows;
+        for (const auto& p : ps) {
             for (int l = 0; l < p.r; ++l) { rows.push_back(p.n); rows.push_back(p.m); }
-        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk : sweep_rows_per_chunk<T, S, C>(rows, o.ortho);
+            grows.push_back(p.n);
+            grows.push_back(p.m);
+        }
+        rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk
+              : o.inner == SYLV_INNER_BICGSTAB ? bicg_rows_per_chunk<T, S, C>(grows)
+                                               : sweep_rows_per_chunk<T, S, C>(rows, o.ortho);
         rpc = (rpc + 31) / 32 * 32;
         // ---- layout of every instance's buffers in one arena ----
         struct Off { size_t f, g, w, t, Z, Y, gam, hist, alpha, beta, pinvA, pinvB, avalA, avalB, gpart; };
@@ -167,7 +294,14 @@ struct Batch : BatchBase {
             }
         }
         eng.ortho = o.ortho;
+        eng.inner = o.inner;
+        eng.restart_every = o.restart_every;
+        driver = o.driver;
+        restart_every = o.restart_every;
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, o.restart, rpc, stream));
+        SYLV_CK(cudaHostAlloc((void**)&h_open, sizeof(int), cudaHostAllocMapped));
+        *h_open = 0;
+        SYLV_CK(cudaHostGetDevicePointer((void**)&d_hopen, h_open, 0));
         SYLV_TRY(st.alloc(count));
         SYLV_CK(cudaMemset(st.p, 0, (size_t)count * sizeof(AdiState<T>)));
         // ---- per-instance descriptors and the outer-kernel work list ----
@@ -270,7 +404,17 @@ struct Batch : BatchBase {
         SYLV_TRY(add_kernel(&n_o, body, nullptr, (void*)k_batch_outer<T, S, C>, nbitems, ao));
         SYLV_TRY(add_kernel(&n_s, body, &n_o, (void*)k_batch_step<T, S, C>, nbitems, ao));
         const int sm = sweep_smem_bytes<S, C>();
-        if (eng.ortho == 1) {
+        auto* grp = eng.d_groups.p;
+        auto* gip = eng.d_gitems.p;
+        int ngi = eng.ngitems;
+        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &ctp};
+        void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
+        void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
+        if (eng.inner == 1) {
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba));
+            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, ba));
+            SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_bicg_c<T, S, C>, ngi, bc));
+        } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, dcgs_a_smem_bytes<T, S, C>()));
             SYLV_TRY(add_kernel(&n3, body, &n1, (void*)k_dcgs_b<T, S, C>, ni + nsysb, ab, dcgs_b_smem_bytes<T, S, C>()));
         } else {
@@ -286,8 +430,12 @@ struct Batch : BatchBase {
         SYLV_CK(cudaGraphAddNode(&n_if, body, &n3, nullptr, 1, &ip));
         cudaGraph_t if_body = ip.conditional.phGraph_out[0];
         const int rg = eng.restart_grid();
-        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, a4));
-        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, a5));
+        if (eng.inner == 1) {
+            SYLV_TRY(add_kernel(&n5, if_body, nullptr, (void*)k_bicg_resid<T, S, C>, rg, br));
+        } else {
+            SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, a4));
+            SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, a5));
+        }
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
         BatchCtl c{};
         SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
@@ -299,6 +447,7 @@ struct Batch : BatchBase {
     }
 
     int solve() override {
+        if (driver == 1 || eng.profile) return solve_host();
         if (!gexec) SYLV_TRY(build_graph());
         // fresh outer states; the control block's counters for this launch
         SYLV_CK(cudaMemsetAsync(st.p, 0, (size_t)count * sizeof(AdiState<T>), stream));
@@ -324,6 +473,11 @@ struct Batch : BatchBase {
         for (int q = 0; q < K_COUNT; ++q) l1 += c.launch_count[q];
         launches_last = (long long)(l1 - l0);
         ticks_last = c.ticks;
+        return finish();
+    }
+
+    // Per-instance status of the finished solve (SYLV_OK or the first failure).
+    int finish() {
         std::vector<AdiState<T>> hs(count);
         SYLV_CK(cudaMemcpy(hs.data(), st.p, (size_t)count * sizeof(AdiState<T>), cudaMemcpyDeviceToHost));
         solved = 1;

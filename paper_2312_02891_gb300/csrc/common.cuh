@@ -20,7 +20,7 @@
 #define SYLV_MR 30                 // maximum GMRES restart length
 #endif
 #define SYLV_MAXV (SYLV_MR + 1)    // basis vectors per cycle
-#define SYLV_MAXDIAG 8             // diagonals of a stencil-stored operator
+#define SYLV_MAXDIAG 9             // diagonals of a stencil-stored operator (2D Q1 mass: 9)
 #define SYLV_BLOCK 256             // threads per block of the vector kernels
 #define SYLV_NWARP (SYLV_BLOCK / 32)
 
@@ -70,6 +70,9 @@ HD cflt operator*(float s, cflt a) { return {s * a.x, s * a.y}; }
 HD cflt operator*(cflt a, float s) { return {s * a.x, s * a.y}; }
 HD cflt& operator+=(cflt& a, cflt b) { a.x += b.x; a.y += b.y; return a; }
 HD cflt& operator-=(cflt& a, cflt b) { a.x -= b.x; a.y -= b.y; return a; }
+
+HD cplx to_cplx(double a) { return {a, 0.0}; }
+HD cplx to_cplx(cplx a) { return a; }
 
 HD cplx cdiv(cplx a, cplx b) {
     // a / b by Smith's method (R. L. Smith, CACM 1962) to avoid overflow.
@@ -179,13 +182,37 @@ struct OpDesc {
     const double* val;
     const double* diag;             // main diagonal (Jacobi)
     long long nnz;                  // nonzeros of the matrix (algorithmic byte counts)
+    // mass matrix of the generalized equation (eq. (gsylv)): the shifted
+    // operator is Op + sigma Mass; all null for Mass = I
+    const double* mval;             // by diagonals, on the offsets of the operator (fmt 1)
+    const int* mrowptr;             // CSR (fmt 0)
+    const int* mcolind;
+    const double* mvalc;
+    const double* mdiag;            // main diagonal of Mass (Jacobi)
+    long long mnnz;
 };
 
-// y_i = sum_j Op[i][j] * X(j) + sigma * X(i), X(k) supplied by the caller.
+// y_i = sum_j Op[i][j] * X(j) + sigma * (Mass X)(i), X(k) supplied by the
+// caller (Mass = I unless the operator carries a mass matrix).
 template <typename T, typename XF>
 __device__ __forceinline__ T op_row(const OpDesc& op, int i, T sigma, XF X) {
     T acc = zero<T>();
     if (op.fmt == 1) {
+        if (op.mval) {
+            T macc = zero<T>();
+#pragma unroll
+            for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+                if (d < op.ndiag) {
+                    int k = i + op.offs[d];
+                    if (k >= 0 && k < op.n) {
+                        const T x = X(k);
+                        acc += op.dval[(size_t)d * op.n + i] * x;
+                        macc += op.mval[(size_t)d * op.n + i] * x;
+                    }
+                }
+            }
+            return acc + sigma * macc;
+        }
 #pragma unroll
         for (int d = 0; d < SYLV_MAXDIAG; ++d) {
             if (d < op.ndiag) {
@@ -196,8 +223,41 @@ __device__ __forceinline__ T op_row(const OpDesc& op, int i, T sigma, XF X) {
     } else {
         int p0 = op.rowptr[i], p1 = op.rowptr[i + 1];
         for (int p = p0; p < p1; ++p) acc += op.val[p] * X(op.colind[p]);
+        if (op.mvalc) {
+            T macc = zero<T>();
+            for (int p = op.mrowptr[i]; p < op.mrowptr[i + 1]; ++p) macc += op.mvalc[p] * X(op.mcolind[p]);
+            return acc + sigma * macc;
+        }
     }
     return acc + sigma * X(i);
+}
+
+// (Mass X)(i) (X(i) when the operator carries no mass matrix).
+template <typename T, typename XF>
+__device__ __forceinline__ T mass_row(const OpDesc& op, int i, XF X) {
+    if (op.fmt == 1 && op.mval) {
+        T acc = zero<T>();
+#pragma unroll
+        for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+            if (d < op.ndiag) {
+                int k = i + op.offs[d];
+                if (k >= 0 && k < op.n) acc += op.mval[(size_t)d * op.n + i] * X(k);
+            }
+        }
+        return acc;
+    }
+    if (op.fmt == 0 && op.mvalc) {
+        T acc = zero<T>();
+        for (int p = op.mrowptr[i]; p < op.mrowptr[i + 1]; ++p) acc += op.mvalc[p] * X(op.mcolind[p]);
+        return acc;
+    }
+    return X(i);
+}
+
+// diag(Op) + sigma diag(Mass) at row i: the Jacobi preconditioner.
+template <typename T>
+__device__ __forceinline__ T shifted_diag(const OpDesc& op, int i, T sigma) {
+    return op.diag[i] + sigma * (op.mdiag ? op.mdiag[i] : 1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -220,9 +280,11 @@ struct SysDesc {
     T* part;                // nchunks x PSTRIDE partial sums
     const T* pinv;          // Jacobi: 1 / (diag + sigma), or null
     const C* aval;          // stencil operators: (Op + sigma I) P^{-1} by diagonals, C precision
-    double* hist;           // optional: Givens estimate per Arnoldi step
+    double* hist;           // optional: Givens estimate (GMRES) or recurrence residual (BiCGstab) per step
     int hist_cap;
     int restart;
+    C* bv;                  // BiCGstab: the system's vectors (BVec order), ldv apart; null for GMRES
+    const C* rres;          // BiCGstab: the last true residual (column-major); null: slot 0 of V
 };
 
 // Basis addressing.  Tile-major (LAY 1, the solver's own basis): rows are
@@ -282,6 +344,12 @@ struct SysState {
     T fvy;                  //   v_j^* y,
     T fs[SYLV_MAXV];        //   s = V^* u_j (scaled),
     T fz[SYLV_MAXV];        //   z = V^* y (scaled)
+    // BiCGstab: rho = rhat^* r of the current residual, the step's alpha and
+    // omega, beta of the next search direction; bfin: the step ended early
+    // (||s|| met the tolerance, omega = 0)
+    T brho, balpha, bomega, bbeta;
+    int bfin;
+    double bnorm0;          // BiCGstab: residual norm at the start of the cycle
 };
 
 // Work item of a launch: (system, chunk).
@@ -308,6 +376,7 @@ struct BatchCtl {
     cudaGraphConditionalHandle h_outer;    // WHILE: outer steps of Algorithm 1
     unsigned long long launch_count[K_COUNT];  // launches, counted by block 0 of each kernel
     int n_inst_open;        // batched solves: instances not finished (0 for a single solve)
+    int* h_open;            // batched solves, host-driven: mapped host word cleared when n_inst_open reaches 0
     int nitems;             // work items of the batch (grid-stride kernels)
 };
 

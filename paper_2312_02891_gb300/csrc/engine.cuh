@@ -7,7 +7,7 @@
 #include <cstring>
 #include <vector>
 #include "internal.h"
-#include "adi_kernels.cuh"
+#include "pair_kernels.cuh"
 
 namespace sylv {
 
@@ -94,6 +94,54 @@ int sweep_rows_per_chunk(const std::vector<long long>& sys_rows, int ortho) {
     return (int)(chunks(fit) <= items ? fit : rpc);
 }
 
+// Rows per work item of the BiCGstab kernels (one item = a row chunk of a
+// group of column systems): one wave of resident blocks of k_bicg_a over the
+// rows of all groups, widened as for the sweeps so that every chunk of the
+// wave has a slot.
+template <typename T, typename S, typename C>
+int bicg_rows_per_chunk(const std::vector<long long>& group_rows) {
+    long long total_rows = 0;
+    for (long long q : group_rows) total_rows += q;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicg_a<T, S, C>, SYLV_BLOCK, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long items = (long long)num_sms() * per_sm;
+    long long rpc = (total_rows + items - 1) / items;
+    rpc = std::max<long long>(256, std::min<long long>((rpc + 31) / 32 * 32, 1 << 16));
+    auto chunks = [&](long long c) {
+        long long k = 0;
+        for (long long q : group_rows) k += (q + c - 1) / c;
+        return k;
+    };
+    long long fit = rpc;
+    while (chunks(fit) > items && fit + 32 <= std::min<long long>(rpc + rpc / 4, 1 << 16)) fit += 32;
+    return (int)(chunks(fit) <= items ? fit : rpc);
+}
+
+// Rows of the BiCGstab groups formed from consecutive column systems with the
+// same rows, operator, Jacobi inverse and stencil values (at most BG_MAXCOL
+// columns each): the partition Engine::setup uses.
+template <typename P1, typename P2>
+std::vector<std::pair<int, int>> bicg_groups(const std::vector<int>& sys_n, const std::vector<int>& sys_op,
+                                             const std::vector<P1>& pinv, const std::vector<P2>& aval) {
+    std::vector<std::pair<int, int>> g;    // (first system, columns)
+    for (int q = 0; q < (int)sys_n.size(); ++q) {
+        const P2 aq = aval.empty() ? P2() : aval[q];
+        if (!g.empty()) {
+            const int f = g.back().first;
+            const P2 af = aval.empty() ? P2() : aval[f];
+            if (g.back().second < BG_MAXCOL && sys_n[f] == sys_n[q] && sys_op[f] == sys_op[q] && pinv[f] == pinv[q] &&
+                af == aq) {
+                g.back().second++;
+                continue;
+            }
+        }
+        g.push_back({q, 1});
+    }
+    return g;
+}
+
 // Elements of one system's tile-major basis: whole 32-row tiles.
 template <class D>
 inline size_t basis_elems(const D& d) { return (size_t)((d.n + 31) / 32) * d.tstride; }
@@ -122,6 +170,15 @@ struct Engine {
     int pending[4] = {0, 0, 0, 0};
     int pkid[4][5] = {};                // kernel id of each timed interval
     int ortho = 0;                      // 0: CGS2 (three sweeps), 1: delayed CGS2 (two sweeps)
+    int inner = 0;                      // 0: restarted GMRES, 1: BiCGstab
+    // BiCGstab: groups of column systems, their work items and vectors
+    int ngroups = 0, ngitems = 0;
+    std::vector<BGroup<T>> h_groups;
+    Dev<BGroup<T>> d_groups;
+    Dev<Item> d_gitems;
+    Dev<C> d_bv;
+    Dev<T> d_gpart;
+    Dev<unsigned> d_gcount;
     int restart_every = 1;              // host driver: restart kernels every k-th device iteration
     double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
     long long samples[K_COUNT] = {};    // sampled launches
@@ -152,9 +209,17 @@ struct Engine {
         restart = restart_;
         nsys = (int)sys_n.size();
         SYLV_TRY((sweep_kernel_setup<T, S, C>()));
-        if (rpc <= 0) rpc = sweep_rows_per_chunk<T, S, C>(std::vector<long long>(sys_n.begin(), sys_n.end()), ortho);
+        if (rpc <= 0) {
+            if (inner == 1) {
+                std::vector<long long> grows;
+                for (const auto& g : bicg_groups(sys_n, sys_op, pinv, aval)) grows.push_back(sys_n[g.first]);
+                rpc = bicg_rows_per_chunk<T, S, C>(grows);
+            } else {
+                rpc = sweep_rows_per_chunk<T, S, C>(std::vector<long long>(sys_n.begin(), sys_n.end()), ortho);
+            }
+        }
         rpc = (rpc + 31) / 32 * 32;       // chunks hold whole 32-row basis tiles
-        size_t vtot = 0, wtot = 0, ptot = 0;
+        size_t vtot = 0, wtot = 0, ptot = 0, btot = 0;
         std::vector<Item> items;
         h_sd.resize(nsys);
         for (int q = 0; q < nsys; ++q) {
@@ -171,8 +236,12 @@ struct Engine {
             d.hist = hist.empty() ? nullptr : hist[q];
             d.hist_cap = hist_cap;
             d.pinv = pinv[q];
-            vtot += basis_elems(d);
-            wtot += d.ldv;
+            if (inner == 1) {
+                btot += (size_t)BV_COUNT * d.ldv;       // no Krylov basis, no work vector
+            } else {
+                vtot += basis_elems(d);
+                wtot += d.ldv;
+            }
             ptot += (size_t)d.nchunks * PSTRIDE;
             for (int c = 0; c < d.nchunks; ++c) items.push_back({q, c});
         }
@@ -180,15 +249,52 @@ struct Engine {
         SYLV_TRY(d_V.alloc(vtot));
         SYLV_TRY(d_w.alloc(wtot));
         SYLV_TRY(d_part.alloc(ptot));
-        size_t vo = 0, wo = 0, po = 0;
+        SYLV_TRY(d_bv.alloc(btot));
+        if (btot) SYLV_CK(cudaMemset(d_bv.p, 0, btot * sizeof(C)));
+        size_t vo = 0, wo = 0, po = 0, bo = 0;
         for (int q = 0; q < nsys; ++q) {
             SysDesc<T, S, C>& d = h_sd[q];
-            d.V = d_V.p + vo;
-            d.w = d_w.p + wo;
+            if (inner == 1) {
+                d.bv = d_bv.p + bo;
+                d.rres = d.bv + (size_t)BV_R * d.ldv;
+                bo += (size_t)BV_COUNT * d.ldv;
+            } else {
+                d.V = d_V.p + vo;
+                d.w = d_w.p + wo;
+                vo += basis_elems(d);
+                wo += d.ldv;
+            }
             d.part = d_part.p + po;
-            vo += basis_elems(d);
-            wo += d.ldv;
             po += (size_t)d.nchunks * PSTRIDE;
+        }
+        if (inner == 1) {
+            // groups of consecutive systems sharing rows, operator and shift data;
+            // their vectors are consecutive in d_bv (BV_COUNT * ldv apart)
+            const auto gs = bicg_groups(sys_n, sys_op, pinv, aval);
+            ngroups = (int)gs.size();
+            size_t gp = 0;
+            for (const auto& g : gs) gp += (size_t)h_sd[g.first].nchunks * BG_PSTRIDE;
+            SYLV_TRY(d_gpart.alloc(gp));
+            SYLV_TRY(d_gcount.alloc(ngroups));
+            SYLV_CK(cudaMemset(d_gcount.p, 0, ngroups * sizeof(unsigned)));
+            std::vector<Item> gitems;
+            h_groups.resize(ngroups);
+            gp = 0;
+            for (int g = 0; g < ngroups; ++g) {
+                BGroup<T>& bg = h_groups[g];
+                bg.sys0 = gs[g].first;
+                bg.ncol = gs[g].second;
+                bg.nchunks = h_sd[bg.sys0].nchunks;
+                bg.part = d_gpart.p + gp;
+                bg.counter = d_gcount.p + g;
+                gp += (size_t)bg.nchunks * BG_PSTRIDE;
+                for (int c = 0; c < bg.nchunks; ++c) gitems.push_back({g, c});
+            }
+            ngitems = (int)gitems.size();
+            SYLV_TRY(d_groups.alloc(ngroups));
+            SYLV_TRY(d_gitems.alloc(gitems.size()));
+            SYLV_CK(cudaMemcpy(d_groups.p, h_groups.data(), ngroups * sizeof(BGroup<T>), cudaMemcpyHostToDevice));
+            SYLV_CK(cudaMemcpy(d_gitems.p, gitems.data(), gitems.size() * sizeof(Item), cudaMemcpyHostToDevice));
         }
         SYLV_TRY(d_sd.alloc(nsys));
         SYLV_TRY(d_st.alloc(nsys));
@@ -199,7 +305,7 @@ struct Engine {
         SYLV_CK(cudaMemcpy(d_items.p, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
         SYLV_CK(cudaMemcpy(d_ops.p, ops.data(), ops.size() * sizeof(OpDesc), cudaMemcpyHostToDevice));
         SYLV_CK(cudaMemset(d_st.p, 0, nsys * sizeof(SysState<T>)));
-        SYLV_CK(cudaMemset(d_V.p, 0, vtot * sizeof(S)));
+        if (vtot) SYLV_CK(cudaMemset(d_V.p, 0, vtot * sizeof(S)));
         SYLV_CK(cudaHostAlloc((void**)&h_flag, sizeof(int), cudaHostAllocMapped));
         *h_flag = 0;
         SYLV_CK(cudaHostGetDevicePointer((void**)&d_hflag, h_flag, 0));
@@ -212,7 +318,7 @@ struct Engine {
     }
 
     // Blocks of the restart kernels (grid-stride over the work items).
-    int restart_grid() const { return std::max(1, std::min(nitems, 2 * num_sms())); }
+    int restart_grid() const { return std::max(1, std::min(inner == 1 ? ngitems : nitems, 2 * num_sms())); }
 
     // A kernel of the device iteration, launched with programmatic stream
     // serialization (the kernel waits for its predecessor in pdl_enter());
@@ -257,6 +363,23 @@ struct Engine {
             launches[kid]++;
             return SYLV_OK;
         };
+        if (inner == 1) {
+            const dim3 g(ngitems);
+            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, 0, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(mark(K_SPMV));
+            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, 0, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(mark(K_CGS2));
+            SYLV_TRY(launch(k_bicg_c<T, S, C>, g, 0, d_sd.p, d_st.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(mark(K_CGS3));
+            if (with_restart) {
+                SYLV_TRY(launch(k_bicg_resid<T, S, C>, dim3(restart_grid()), 0, d_sd.p, d_st.p, d_ops.p, d_groups.p,
+                                d_gitems.p, ngitems, d_ctl.p));
+                SYLV_TRY(mark(K_RRES));
+            }
+            if (pe) pending[slot] = nk;
+            SYLV_CK(cudaGetLastError());
+            return SYLV_OK;
+        }
         if (ortho == 1 && cgs_mode == 0) {
             SYLV_TRY(launch(k_dcgs_a<T, S, C>, grid, dcgs_a_smem_bytes<T, S, C>(), d_sd.p, d_st.p, d_ops.p,
                             d_items.p, d_ctl.p));
@@ -371,7 +494,7 @@ __global__ void k_op_apply(OpDesc op, T sigma, int jacobi, const T* __restrict__
         T y;
         if (jacobi)
             y = op_row<T>(op, i, sigma, [&](int k) {
-                return sdiv(make_scalar<T>(1.0, 0.0), op.diag[k] + sigma) * x[k];
+                return sdiv(make_scalar<T>(1.0, 0.0), shifted_diag(op, k, sigma)) * x[k];
             });
         else
             y = op_row<T>(op, i, sigma, [&](int k) { return x[k]; });
@@ -427,15 +550,20 @@ int shifted_op_setup(const OpDesc& op, T sigma, T* pinv, C* aval, cudaStream_t s
     return SYLV_OK;
 }
 
+// Batched shifted solves of one operator: restarted GMRES (inner = 0) or
+// BiCGstab (inner = 1, restart unused).
 template <typename T, typename S, typename C>
-int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
-            int restart, int max_iters, int* iters, double* res, double* hist, cudaStream_t s) {
+int krylov_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
+             int restart, int max_iters, int* iters, double* res, double* hist, cudaStream_t s, int inner) {
+    const char* name = inner == 1 ? "bicgstab" : "gmres";
+    if (inner == 1) restart = 1;
     if (!B || !X || ncols <= 0 || restart < 1 || restart > SYLV_MR || max_iters < 1) {
-        set_error("gmres: invalid arguments (ncols=%d restart=%d max_iters=%d)", ncols, restart, max_iters);
+        set_error("%s: invalid arguments (ncols=%d restart=%d max_iters=%d)", name, ncols, restart, max_iters);
         return SYLV_ERR_INVALID;
     }
     const int n = op.desc.n;
     Engine<T, S, C> eng;
+    eng.inner = inner;
     Dev<T> pinv;
     Dev<C> aval;
     Dev<double> d_hist;
@@ -488,8 +616,102 @@ int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int nc
                 hist[(size_t)c * max_iters + i] = i < st[c].iters ? hh[(size_t)c * max_iters + i] : 0.0;
     }
     for (int c = 0; c < ncols; ++c)
-        if (st[c].status == ST_NONFINITE) { set_error("gmres: non-finite value in column %d", c); return SYLV_ERR_NONFINITE; }
-    if (stalled) { set_error("gmres: a column reached max_iters"); return SYLV_ERR_INNER_STALL; }
+        if (st[c].status == ST_NONFINITE) { set_error("%s: non-finite value in column %d", name, c); return SYLV_ERR_NONFINITE; }
+    if (stalled) { set_error("%s: a column reached max_iters", name); return SYLV_ERR_INNER_STALL; }
+    return SYLV_OK;
+}
+
+template <typename T, typename S, typename C>
+int gmres_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
+            int restart, int max_iters, int* iters, double* res, double* hist, cudaStream_t s) {
+    return krylov_t<T, S, C>(op, sigma, jacobi, B, X, ncols, tol, restart, max_iters, iters, res, hist, s, 0);
+}
+
+template <typename T, typename S, typename C>
+int bicgstab_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int ncols, double tol,
+               int max_iters, int* iters, double* res, double* hist, cudaStream_t s) {
+    return krylov_t<T, S, C>(op, sigma, jacobi, B, X, ncols, tol, 1, max_iters, iters, res, hist, s, 1);
+}
+
+// Column col of a tile-major basis (storage S) times scale, as T.
+template <typename T, typename S>
+__global__ void k_basis_column(const S* __restrict__ V, size_t tstride, int col, double scale, T* __restrict__ dst,
+                               int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = scale * cvt<T>(V[(size_t)(i >> 5) * tstride + (size_t)col * 32 + (i & 31)]);
+}
+
+// v (T, length n) into slot 0 of a tile-major basis of storage S.
+template <typename T, typename S>
+__global__ void k_basis_set0(const T* __restrict__ v, int n, S* __restrict__ V, size_t tstride) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        V[(size_t)(i >> 5) * tstride + (i & 31)] = cvt<S>(v[i]);
+}
+
+// One Arnoldi cycle of k steps of the inner GMRES, as the solver runs it
+// (precision S/C, CGS2 or delayed CGS2, right Jacobi): v0 (device, T) is the
+// start vector; V_out (device, n x (k + 1), T) receives the basis vectors
+// v_0 .. v_k as scale x stored vector (with DCGS2 v_k is not completed by
+// the cycle and is left zero), H_out (host, (k + 1) x k, T, column-major) the
+// Hessenberg matrix as formed.
+template <typename T, typename S, typename C>
+int arnoldi_t(const DevOp& op, T sigma, int jacobi, const void* v0, int k, int ortho, void* V_out, void* H_out,
+              cudaStream_t s) {
+    if (!v0 || !V_out || !H_out || k < 1 || k > SYLV_MR || (ortho != 0 && ortho != 1)) {
+        set_error("arnoldi: invalid arguments (k=%d, 1 <= k <= %d, ortho=%d)", k, SYLV_MR, ortho);
+        return SYLV_ERR_INVALID;
+    }
+    const int n = op.desc.n;
+    Engine<T, S, C> eng;
+    eng.ortho = ortho;
+    Dev<T> pinv;
+    Dev<C> aval;
+    if (jacobi) SYLV_TRY(pinv.alloc(n));
+    if (scaled_op_possible(op.desc)) SYLV_TRY(aval.alloc((size_t)op.desc.ndiag * n));
+    const std::vector<int> sn{n}, so{0};
+    const std::vector<T*> pv{jacobi ? pinv.p : nullptr};
+    const std::vector<C*> av{aval.p};
+    std::vector<OpDesc> ops{op.desc};
+    SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, k, 0, s));
+    SYLV_TRY((shifted_op_setup<T, C>(op.desc, sigma, pinv.p, aval.p, s)));
+    const SysDesc<T, S, C>& d = eng.h_sd[0];
+    k_basis_set0<T, S><<<num_sms() * 4, 256, 0, s>>>((const T*)v0, n, d.V, d.tstride);
+    SYLV_CK(cudaGetLastError());
+    SysState<T> st;
+    std::memset(&st, 0, sizeof(st));
+    st.phase = PH_ARNOLDI;
+    st.j = 0;
+    st.scale[0] = 1.0;
+    st.g[0] = make_scalar<T>(1.0, 0.0);
+    st.tol = 0.0;                         // the cycle runs to its restart length
+    st.max_iters = k;
+    st.sigma = sigma;
+    SYLV_CK(cudaMemcpyAsync(eng.d_st.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    BatchCtl c{};
+    c.n_active = 1;
+    c.h_flag = eng.d_hflag;
+    c.nitems = eng.nitems;
+    SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+    // k steps (CGS2), k + 1 device iterations with the delayed second pass;
+    // iterations after the cycle's end find the system in the update phase
+    for (int t = 0; t < k + 1; ++t) SYLV_TRY(eng.launch_tick(0, 0, false));
+    SYLV_CK(cudaStreamSynchronize(s));
+    SYLV_CK(cudaMemcpy(&st, eng.d_st.p, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.phase != PH_UPDATE || st.nvec != k) {
+        set_error("arnoldi: the cycle ended after %d of %d steps (breakdown or non-finite value)", st.nvec, k);
+        return SYLV_ERR_NONFINITE;
+    }
+    T* Vo = (T*)V_out;
+    SYLV_CK(cudaMemsetAsync(Vo, 0, (size_t)n * (k + 1) * sizeof(T), s));
+    const int last = ortho == 1 ? k - 1 : k;
+    for (int l = 0; l <= last; ++l) {
+        k_basis_column<T, S><<<num_sms() * 4, 256, 0, s>>>(d.V, d.tstride, l, st.scale[l], Vo + (size_t)l * n, n);
+        SYLV_CK(cudaGetLastError());
+    }
+    SYLV_CK(cudaStreamSynchronize(s));
+    T* ho = (T*)H_out;
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i <= k; ++i) ho[(size_t)j * (k + 1) + i] = i <= j + 1 ? st.Hr[j * SYLV_MAXV + i] : zero<T>();
     return SYLV_OK;
 }
 
@@ -545,6 +767,10 @@ struct Adi : AdiBase {
     Dev<T> w, t, Z, Y, gam, alpha, beta, pinvA, pinvB, gpart;
     Dev<C> avalA, avalB;
     Dev<AdiState<T>> st;
+    // real double steps of conjugate pairs (complex shifts, opts.real_pairs)
+    int real_pairs = 0;
+    Dev<T> XA, XB, XA2, XB2;
+    Dev<double> Zr, Yr, core_rec, RsA, RsB, pgpart;
     int* h_done = nullptr;
     int* d_hdone = nullptr;
     int solved = 0;
@@ -580,16 +806,36 @@ struct Adi : AdiBase {
         n = a.n; m = a.m; r = a.r; kmax = a.o.kmax; max_inner = a.o.max_inner;
         std::vector<long long> rows;
         for (int l = 0; l < r; ++l) { rows.push_back(n); rows.push_back(m); }
+        // BiCGstab: the r columns of each side form one group
+        const std::vector<long long> grows{(long long)n, (long long)m};
         const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
-                                               : sweep_rows_per_chunk<T, S, C>(rows, a.o.ortho);
+                        : a.o.inner == SYLV_INNER_BICGSTAB ? bicg_rows_per_chunk<T, S, C>(grows)
+                                                           : sweep_rows_per_chunk<T, S, C>(rows, a.o.ortho);
+        real_pairs = (a.o.real_pairs && sizeof(T) == sizeof(cplx)) ? 1 : 0;
+        // a pair that starts at step kmax ends at kmax + 1
+        const int ksl = kmax + real_pairs;
         SYLV_TRY(f.alloc((size_t)n * r));
         SYLV_TRY(g.alloc((size_t)m * r));
         SYLV_TRY(w.alloc((size_t)n * r));
         SYLV_TRY(t.alloc((size_t)m * r));
-        SYLV_TRY(Z.alloc((size_t)n * r * kmax));
-        SYLV_TRY(Y.alloc((size_t)m * r * kmax));
+        if (real_pairs) {
+            // real factors; the solves write complex work blocks
+            SYLV_TRY(Zr.alloc((size_t)n * r * ksl));
+            SYLV_TRY(Yr.alloc((size_t)m * r * ksl));
+            SYLV_TRY(core_rec.alloc((size_t)ksl * 5));
+            SYLV_TRY(XA.alloc((size_t)n * r));
+            SYLV_TRY(XB.alloc((size_t)m * r));
+            SYLV_TRY(XA2.alloc((size_t)n * r));
+            SYLV_TRY(XB2.alloc((size_t)m * r));
+            SYLV_TRY(RsA.alloc((size_t)n * r));
+            SYLV_TRY(RsB.alloc((size_t)m * r));
+            SYLV_CK(cudaMemset(core_rec.p, 0, core_rec.count * sizeof(double)));
+        } else {
+            SYLV_TRY(Z.alloc((size_t)n * r * kmax));
+            SYLV_TRY(Y.alloc((size_t)m * r * kmax));
+        }
         SYLV_TRY(gam.alloc((size_t)r * kmax));
-        SYLV_TRY(hist.alloc((size_t)kmax * SYLV_HIST_COLS));
+        SYLV_TRY(hist.alloc((size_t)ksl * SYLV_HIST_COLS));
         SYLV_TRY(alpha.alloc(a.nshift));
         SYLV_TRY(beta.alloc(a.nshift));
         if (a.o.jacobi) {
@@ -600,8 +846,8 @@ struct Adi : AdiBase {
         if (scaled_op_possible(a.Bt->desc)) SYLV_TRY(avalB.alloc((size_t)a.Bt->desc.ndiag * m));
         SYLV_TRY(st.alloc(1));
         SYLV_CK(cudaMemset(st.p, 0, sizeof(AdiState<T>)));
-        SYLV_CK(cudaMemset(Z.p, 0, Z.count * sizeof(T)));
-        SYLV_CK(cudaMemset(Y.p, 0, Y.count * sizeof(T)));
+        if (Z.p) SYLV_CK(cudaMemset(Z.p, 0, Z.count * sizeof(T)));
+        if (Y.p) SYLV_CK(cudaMemset(Y.p, 0, Y.count * sizeof(T)));
         SYLV_CK(cudaMemset(hist.p, 0, hist.count * sizeof(double)));
         std::vector<T> ha(a.nshift), hb(a.nshift);
         for (int i = 0; i < a.nshift; ++i) {
@@ -619,9 +865,11 @@ struct Adi : AdiBase {
         for (int l = 0; l < r; ++l) { sn.push_back(m); so.push_back(1); pv.push_back(pinvB.p); av.push_back(avalB.p); }
         std::vector<OpDesc> ops{a.A->desc, a.Bt->desc};
         eng.ortho = a.o.ortho;
+        eng.inner = a.o.inner;
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, a.o.restart, rpc, stream));
         const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
         SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
+        if (real_pairs) SYLV_TRY(pgpart.alloc((size_t)(nchA + nchB) * SYLV_PGSTRIDE));
         SYLV_CK(cudaHostAlloc((void**)&h_done, sizeof(int), cudaHostAllocMapped));
         *h_done = 0;
         SYLV_CK(cudaHostGetDevicePointer((void**)&d_hdone, h_done, 0));
@@ -639,6 +887,9 @@ struct Adi : AdiBase {
         d.sd = eng.d_sd.p; d.st = eng.d_st.p; d.ctl = eng.d_ctl.p;
         d.gpart = gpart.p; d.nchA = nchA; d.nchB = nchB; d.rpc = rpc;
         d.s = st.p; d.h_done = d_hdone;
+        d.real_pairs = real_pairs;
+        d.XA = XA.p; d.XB = XB.p; d.XA2 = XA2.p; d.XB2 = XB2.p;
+        d.Zr = Zr.p; d.Yr = Yr.p; d.core = core_rec.p; d.RsA = RsA.p; d.RsB = RsB.p; d.pgpart = pgpart.p;
         graph_on = a.o.driver == 0 ? 1 : 0;
         eng.restart_every = a.o.restart_every;
         return SYLV_OK;
@@ -742,7 +993,17 @@ struct Adi : AdiBase {
         void* a4[] = {&sdp, &stp, &itp, &ctp};
         void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
         const int sm = sweep_smem_bytes<S, C>();
-        if (eng.ortho == 1) {
+        auto* grp = eng.d_groups.p;
+        auto* gip = eng.d_gitems.p;
+        int ngi = eng.ngitems;
+        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &ctp};
+        void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
+        void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
+        if (eng.inner == 1) {
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba));
+            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, ba));
+            SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_bicg_c<T, S, C>, ngi, SYLV_BLOCK, bc));
+        } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5,
                                 dcgs_a_smem_bytes<T, S, C>()));
             SYLV_TRY(add_kernel(&n3, loop_body, &n1, (void*)k_dcgs_b<T, S, C>, ni + nsysb, SYLV_BLOCK, ab,
@@ -754,8 +1015,12 @@ struct Adi : AdiBase {
         }
         SYLV_TRY(add_cond(&n_if, loop_body, &n3, h_restart, cudaGraphCondTypeIf, &if_body));
         const int rg = eng.restart_grid();
-        SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, SYLV_BLOCK, a4));
-        SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, SYLV_BLOCK, a5));
+        if (eng.inner == 1) {
+            SYLV_TRY(add_kernel(&n5, if_body, nullptr, (void*)k_bicg_resid<T, S, C>, rg, SYLV_BLOCK, br));
+        } else {
+            SYLV_TRY(add_kernel(&n4, if_body, nullptr, (void*)k_restart_update<T, S, C>, rg, SYLV_BLOCK, a4));
+            SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, SYLV_BLOCK, a5));
+        }
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
         // the kernels read the handles and the decision parameters from the control block
         BatchCtl c{};
@@ -805,8 +1070,92 @@ struct Adi : AdiBase {
     }
 
     int solve() override {
+        if (real_pairs) return solve_pairs();
         if (graph_on && !eng.profile) return solve_graph();
         return solve_host();
+    }
+
+    int launch_pair_update(int nb) {
+        switch (r) {
+            case 1: k_adi_pair_update<T, S, C, 1><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
+            case 2: k_adi_pair_update<T, S, C, 2><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
+            case 3: k_adi_pair_update<T, S, C, 3><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
+            default: k_adi_pair_update<T, S, C, 4><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
+        }
+        SYLV_CK(cudaGetLastError());
+        eng.launches[K_GRAM]++;
+        return SYLV_OK;
+    }
+
+    // Host-driven solve with the real double step of conjugate pairs: per
+    // (double) step, controller -> set-up -> first solves -> pair_mid ->
+    // (second solves of real-shift sides) -> pair update.
+    int solve_pairs() {
+        const int nb = d.nchA + d.nchB;
+        const unsigned long long dl0 = device_launches();
+        *h_done = 0;
+        k_adi_gram<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d, 1);
+        SYLV_CK(cudaGetLastError());
+        eng.launches[K_GRAM]++;
+        long long t0 = eng.ticks;
+        for (int step = 0; step <= kmax + 1; ++step) {
+            SYLV_CK(cudaStreamSynchronize(stream));
+            if (*(volatile int*)h_done) break;
+            *eng.h_flag = 1;
+            k_adi_controller<T, S, C><<<1, 32, 0, stream>>>(d);
+            k_adi_step_init<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+            SYLV_CK(cudaGetLastError());
+            eng.launches[K_CTRL]++; eng.launches[K_STEP]++;
+            SYLV_TRY(eng.run((long long)max_inner + 8));
+            k_adi_pair_mid<T, S, C><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+            SYLV_CK(cudaGetLastError());
+            SYLV_CK(cudaStreamSynchronize(stream));
+            if (*(volatile int*)eng.h_flag) SYLV_TRY(eng.run((long long)max_inner + 8));
+            SYLV_TRY(launch_pair_update(nb));
+        }
+        SYLV_CK(cudaStreamSynchronize(stream));
+        ticks = eng.ticks - t0;
+        return finish_solve(dl0);
+    }
+
+    int is_real() const override { return sizeof(T) == sizeof(double) || real_pairs; }
+
+    int core(double* G, int ld, int* kr) const override {
+        AdiState<T> s;
+        SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));
+        const int steps = solved ? s.k - 1 : 0;
+        const int ncol = steps * r;
+        if (kr) *kr = ncol;
+        if (!is_real()) {
+            set_error("complex factors: the core is the diagonal gamma of sylv_adi_factors");
+            return SYLV_ERR_UNSUPPORTED;
+        }
+        if (!G) return SYLV_OK;
+        if (ld < ncol) { set_error("core: ld %d < kr %d", ld, ncol); return SYLV_ERR_INVALID; }
+        for (int c = 0; c < ncol; ++c)
+            for (int q = 0; q < ncol; ++q) G[q + (size_t)c * ld] = 0.0;
+        if (!real_pairs) {
+            std::vector<double> gh(ncol);
+            if (ncol) SYLV_CK(cudaMemcpy(gh.data(), gam.p, ncol * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int c = 0; c < ncol; ++c) G[c + (size_t)c * ld] = gh[c];
+            return SYLV_OK;
+        }
+        std::vector<double> rec((size_t)std::max(steps, 1) * 5);
+        if (steps) SYLV_CK(cudaMemcpy(rec.data(), core_rec.p, (size_t)steps * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+        int c0 = 0;
+        for (int k = 0; k < steps; ++k) {
+            const double* e = &rec[(size_t)k * 5];
+            if (e[0] == 1.0) {
+                for (int l = 0; l < r; ++l) G[(c0 + l) + (size_t)(c0 + l) * ld] = e[1];
+                c0 += r;
+            } else if (e[0] == 2.0) {
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q)
+                        for (int l = 0; l < r; ++l) G[(c0 + p * r + l) + (size_t)(c0 + q * r + l) * ld] = e[1 + 2 * p + q];
+                c0 += 2 * r;
+            }
+        }
+        return SYLV_OK;
     }
 
     int solve_host() {
@@ -859,7 +1208,7 @@ struct Adi : AdiBase {
         out->status = last_status;
         out->steps = solved ? s.k - 1 : 0;
         out->kr = out->steps * r;
-        out->is_complex = sizeof(T) == sizeof(cplx);
+        out->is_complex = is_real() ? 0 : 1;
         out->rel_res_comp = s.nfg > 0 ? s.res / s.nfg : 0.0;
         out->norm_fg = s.nfg;
         out->inner_its_A = s.itsA;
@@ -887,10 +1236,16 @@ struct Adi : AdiBase {
         const int steps = solved ? s.k - 1 : 0;
         const size_t ncol = (size_t)steps * r;
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (kr) *kr = (int)ncol;
+        if (real_pairs) {
+            if (go) { set_error("real double steps: the core has 2 x 2 blocks, use sylv_adi_core (gamma must be NULL)"); return SYLV_ERR_INVALID; }
+            if (Zo && ncol) SYLV_CK(cudaMemcpy(Zo, Zr.p, ncol * n * sizeof(double), kind));
+            if (Yo && ncol) SYLV_CK(cudaMemcpy(Yo, Yr.p, ncol * m * sizeof(double), kind));
+            return SYLV_OK;
+        }
         if (Zo && ncol) SYLV_CK(cudaMemcpy(Zo, Z.p, ncol * n * sizeof(T), kind));
         if (Yo && ncol) SYLV_CK(cudaMemcpy(Yo, Y.p, ncol * m * sizeof(T), kind));
         if (go && ncol) SYLV_CK(cudaMemcpy(go, gam.p, ncol * sizeof(T), kind));
-        if (kr) *kr = (int)ncol;
         return SYLV_OK;
     }
 };

@@ -574,9 +574,14 @@ __device__ void arnoldi_finish(int restart, double* hist, int hist_cap, SysState
     __shared__ T s_col[SYLV_MAXV];
     __shared__ T s_R[SYLV_MR * SYLV_MAXV];
     const int j = st->j;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = st->h1[i] + st->h2[i];
-    __syncthreads();
     const double hn = sqrt(nrm2);
+    // column j as formed (unrotated) is kept in Hr, as in the delayed variant
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) {
+        const T hi = i <= j ? st->h1[i] + st->h2[i] : make_scalar<T>(hn, 0.0);
+        if (i <= j) s_col[i] = hi;
+        st->Hr[j * SYLV_MAXV + i] = hi;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) st->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     const int end = hess_column_finish<T>(restart, hist, hist_cap, st, j, s_col, hn, s_R);
     if (end == 0 && threadIdx.x == 0) st->j = j + 1;
@@ -1368,15 +1373,16 @@ k_zero_x(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 template <typename T, typename C>
 __device__ __forceinline__ void shifted_op_rows(const OpDesc& op, T sigma, T* pinv, C* aval, int r0, int r1) {
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        if (pinv) pinv[i] = sdiv(make_scalar<T>(1.0, 0.0), op.diag[i] + sigma);
+        if (pinv) pinv[i] = sdiv(make_scalar<T>(1.0, 0.0), shifted_diag(op, i, sigma));
         if (!aval) continue;
         for (int d = 0; d < op.ndiag; ++d) {
             const int k = i + op.offs[d];
             T a = zero<T>();
             if (k >= 0 && k < op.n) {
                 a = make_scalar<T>(op.dval[(size_t)d * op.n + i], 0.0);
-                if (op.offs[d] == 0) a = a + sigma;
-                if (pinv) a = a * sdiv(make_scalar<T>(1.0, 0.0), op.diag[k] + sigma);
+                if (op.mval) a = a + sigma * op.mval[(size_t)d * op.n + i];
+                else if (op.offs[d] == 0) a = a + sigma;
+                if (pinv) a = a * sdiv(make_scalar<T>(1.0, 0.0), shifted_diag(op, k, sigma));
             }
             aval[(size_t)d * op.n + i] = cvt<C>(a);
         }

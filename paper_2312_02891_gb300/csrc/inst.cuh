@@ -34,4 +34,16 @@ int SYLV_CAT(gmres_, SYLV_SUFFIX)(const DevOp& op, sylv_shift sigma, int jacobi,
                                            max_iters, iters, res, hist, s);
 }
 
+int SYLV_CAT(arnoldi_, SYLV_SUFFIX)(const DevOp& op, sylv_shift sigma, int jacobi, const void* v0, int k, int ortho,
+                                    void* V_out, void* H_out, cudaStream_t s) {
+    return arnoldi_t<SYLV_T, SYLV_S, SYLV_C>(op, shift_to<SYLV_T>(sigma), jacobi, v0, k, ortho, V_out, H_out, s);
+}
+
+int SYLV_CAT(bicgstab_, SYLV_SUFFIX)(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,
+                                     int ncols, double tol, int max_iters, int* iters, double* res,
+                                     double* hist, cudaStream_t s) {
+    return bicgstab_t<SYLV_T, SYLV_S, SYLV_C>(op, shift_to<SYLV_T>(sigma), jacobi, B, X, ncols, tol, max_iters,
+                                              iters, res, hist, s);
+}
+
 }  // namespace sylv

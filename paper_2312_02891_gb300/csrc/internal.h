@@ -42,12 +42,19 @@ void transpose_csr(const HostCsr& a, HostCsr& t);
 struct DevOp {
     OpDesc desc{};
     int is_stencil = 0;
+    int has_mass = 0;
     double* d_dval = nullptr;
     int* d_rp = nullptr;
     int* d_ci = nullptr;
     double* d_v = nullptr;
     double* d_diag = nullptr;
-    int upload(const HostCsr& h);
+    double* d_mval = nullptr;       // mass by diagonals
+    int* d_mrp = nullptr;           // mass in CSR
+    int* d_mci = nullptr;
+    double* d_mv = nullptr;
+    double* d_mdiag = nullptr;
+    // the operator, and optionally the mass matrix of Op + sigma Mass (same size)
+    int upload(const HostCsr& h, const HostCsr* mass = nullptr);
     void release();
 };
 
@@ -63,6 +70,8 @@ struct AdiBase {
     virtual int factors(void* Z, void* Y, void* gamma, int on_device, int* kr) const = 0;
     virtual int profile(int on) = 0;
     virtual int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const = 0;
+    virtual int core(double* G, int ld, int* kr) const = 0;
+    virtual int is_real() const = 0;     // factors are real (real shifts or real double steps)
 };
 
 struct AdiArgs {
@@ -102,6 +111,9 @@ struct BatchBase {
     virtual int history(int i, double* buf, int cap, int* rows) const = 0;
     virtual int factors(int i, void* Z, void* Y, void* gamma, int on_device, int* kr) const = 0;
     virtual int stats(long long* launches, double* bytes, double* flops, long long* ticks) const = 0;
+    virtual int profile(int on) = 0;
+    virtual int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const = 0;
+    virtual int set_rhs(int i, const double* f, const double* g) = 0;
 };
 
 // One instantiation per (shift type, precision): r = real shifts, c = complex
@@ -112,6 +124,11 @@ struct BatchBase {
     int gmres_##SUFFIX(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,       \
                        int ncols, double tol, int restart, int max_iters, int* iters, double* res, \
                        double* hist, cudaStream_t s);                                                \
+    int arnoldi_##SUFFIX(const DevOp& op, sylv_shift sigma, int jacobi, const void* v0, int k, int ortho, \
+                         void* V_out, void* H_out, cudaStream_t s);                                \
+    int bicgstab_##SUFFIX(const DevOp& op, sylv_shift sigma, int jacobi, const void* B, void* X,    \
+                          int ncols, double tol, int max_iters, int* iters, double* res, double* hist, \
+                          cudaStream_t s);                                                          \
     int make_batch_##SUFFIX(const std::vector<BatchProb>& ps, const sylv_opts& o, cudaStream_t s,      \
                             BatchBase** out);
 SYLV_DECL_INST(r64)

@@ -10,18 +10,16 @@
 // one file-scope __device__ array of SYLV_NOALLOC_SCRATCH_BYTES bytes, which
 // every GPU that loads this library holds until the process exits.
 #include <cstddef>
-#include <mutex>
 #include "engine.cuh"
 
 namespace sylv {
 
 constexpr size_t kScratchBytes = SYLV_NOALLOC_SCRATCH_BYTES;
 constexpr int kRowsPerChunk = 4096;
-constexpr int kMaxDevices = 64;
 
 // The scratch.  Host code must not pass this name to a kernel: on the host it
 // is only a stand-in for the device array.  Its device address comes from
-// cudaGetSymbolAddress, taken once per device below.
+// cudaGetSymbolAddress, looked up with the device current on each call.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 typedef SysDesc<double, double, double> Desc64;
@@ -42,24 +40,14 @@ struct ScratchLayout {
     }
 };
 
-static unsigned char* g_scratch_dev[kMaxDevices] = {};
-static std::mutex g_scratch_mutex;
-
-// Device address of g_scratch on the current device (set-up on first use).
+// Device address of g_scratch on the current device.  It is looked up on
+// every call (a cheap query): an address cached across calls would go stale
+// if the primary context were torn down and recreated, which reloads the
+// module and may place the array elsewhere.
 static int scratch_address(unsigned char** out) {
-    int dev = 0;
-    SYLV_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("sylv_cgs2_noalloc: device %d outside the supported range", dev);
-        return SYLV_ERR_INVALID;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_dev[dev]) {
-        void* p = nullptr;
-        SYLV_CK(cudaGetSymbolAddress(&p, g_scratch));
-        g_scratch_dev[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_dev[dev];
+    void* p = nullptr;
+    SYLV_CK(cudaGetSymbolAddress(&p, g_scratch));
+    *out = static_cast<unsigned char*>(p);
     return SYLV_OK;
 }
 
@@ -79,12 +67,19 @@ __global__ void k_noalloc_scale(double* __restrict__ v, const State64* __restric
 
 using namespace sylv;
 
+// Largest chunk count whose layout fits the scratch (the layout grows
+// with the chunk count, so a binary search finds it).
+static int max_chunks() {
+    int lo = 0, hi = (int)(kScratchBytes / sizeof(Item)) + 1;     // layout(lo) fits, layout(hi) does not
+    while (hi - lo > 1) {
+        const int mid = lo + (hi - lo) / 2;
+        if (ScratchLayout(mid).total <= kScratchBytes) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 extern "C" int sylv_cgs2_noalloc_max_rows(void) {
-    // largest n whose chunk table and partial sums fit next to the fixed parts
-    const size_t fixed = ScratchLayout(0).part;
-    const size_t per_chunk = sizeof(Item) + sizeof(double) * PSTRIDE + 256;
-    const size_t chunks = (kScratchBytes - fixed) / per_chunk;
-    const size_t rows = chunks * (size_t)kRowsPerChunk;
+    const long long rows = (long long)max_chunks() * kRowsPerChunk;
     return rows > 0x7fffffff ? 0x7fffffff : (int)rows;
 }
 
@@ -95,7 +90,7 @@ extern "C" int sylv_cgs2_noalloc(double* V, int32_t n, int32_t k, const double* 
     }
     const int nchunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
     const ScratchLayout L(nchunks);
-    if (n > sylv_cgs2_noalloc_max_rows() || L.total > kScratchBytes) {
+    if (L.total > kScratchBytes) {
         set_error("sylv_cgs2_noalloc: n=%d exceeds the %d rows its %zu-byte static scratch holds",
                   n, sylv_cgs2_noalloc_max_rows(), (size_t)kScratchBytes);
         return SYLV_ERR_INVALID;

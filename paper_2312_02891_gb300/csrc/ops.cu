@@ -101,65 +101,87 @@ void transpose_csr(const HostCsr& a, HostCsr& t) {
 }
 
 void DevOp::release() {
-    if (d_dval) cudaFree(d_dval);
-    if (d_rp) cudaFree(d_rp);
-    if (d_ci) cudaFree(d_ci);
-    if (d_v) cudaFree(d_v);
-    if (d_diag) cudaFree(d_diag);
-    d_dval = d_v = d_diag = nullptr;
-    d_rp = d_ci = nullptr;
+    for (double** q : {&d_dval, &d_v, &d_diag, &d_mval, &d_mv, &d_mdiag})
+        if (*q) { cudaFree(*q); *q = nullptr; }
+    for (int** q : {&d_rp, &d_ci, &d_mrp, &d_mci})
+        if (*q) { cudaFree(*q); *q = nullptr; }
 }
 
-int DevOp::upload(const HostCsr& h) {
+template <typename X>
+static int to_device(X** dst, const std::vector<X>& src) {
+    if (src.empty()) { *dst = nullptr; return SYLV_OK; }
+    SYLV_CK(cudaMalloc((void**)dst, src.size() * sizeof(X)));
+    SYLV_CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice));
+    return SYLV_OK;
+}
+
+int DevOp::upload(const HostCsr& h, const HostCsr* mass) {
     release();
     const int n = h.n;
-    std::vector<double> diag(n, 0.0);
+    if (mass && mass->n != n) { set_error("mass matrix of size %d for an operator of size %d", mass->n, n); return SYLV_ERR_INVALID; }
+    std::vector<double> diag(n, 0.0), mdiag(mass ? n : 0, 0.0);
+    // offsets of the nonzeros of the operator and of the mass matrix together
     std::map<int, int> offs;
     bool stencil = true;
-    for (int i = 0; i < n; ++i)
-        for (int p = h.rp[i]; p < h.rp[i + 1]; ++p) {
-            const int o = h.ci[p] - i;
-            if (o == 0) diag[i] += h.v[p];
-            if (stencil && !offs.count(o)) {
-                if ((int)offs.size() >= SYLV_MAXDIAG) stencil = false;
-                else offs[o] = 0;
+    auto scan = [&](const HostCsr& c, std::vector<double>& dg) {
+        for (int i = 0; i < n; ++i)
+            for (int p = c.rp[i]; p < c.rp[i + 1]; ++p) {
+                const int o = c.ci[p] - i;
+                if (o == 0) dg[i] += c.v[p];
+                if (stencil && !offs.count(o)) {
+                    if ((int)offs.size() >= SYLV_MAXDIAG) stencil = false;
+                    else offs[o] = 0;
+                }
             }
-        }
+    };
+    scan(h, diag);
+    if (mass) scan(*mass, mdiag);
     desc = OpDesc{};
     desc.n = n;
     desc.nnz = (long long)h.ci.size();
+    desc.mnnz = mass ? (long long)mass->ci.size() : 0;
+    has_mass = mass ? 1 : 0;
     if (stencil) {
         int d = 0;
         for (auto& kv : offs) { kv.second = d; desc.offs[d] = kv.first; ++d; }
         desc.ndiag = d;
         desc.fmt = 1;
-        std::vector<double> dval((size_t)d * n, 0.0);
-        for (int i = 0; i < n; ++i)
-            for (int p = h.rp[i]; p < h.rp[i + 1]; ++p)
-                dval[(size_t)offs[h.ci[p] - i] * n + i] += h.v[p];
-        if (d > 0) {
-            SYLV_CK(cudaMalloc((void**)&d_dval, dval.size() * sizeof(double)));
-            SYLV_CK(cudaMemcpy(d_dval, dval.data(), dval.size() * sizeof(double), cudaMemcpyHostToDevice));
-        }
+        auto by_diag = [&](const HostCsr& c) {
+            std::vector<double> dv((size_t)d * n, 0.0);
+            for (int i = 0; i < n; ++i)
+                for (int p = c.rp[i]; p < c.rp[i + 1]; ++p) dv[(size_t)offs[c.ci[p] - i] * n + i] += c.v[p];
+            return dv;
+        };
+        SYLV_TRY(to_device(&d_dval, by_diag(h)));
         desc.dval = d_dval;
+        if (mass) {
+            SYLV_TRY(to_device(&d_mval, by_diag(*mass)));
+            desc.mval = d_mval;
+        }
     } else {
         desc.fmt = 0;
-        SYLV_CK(cudaMalloc((void**)&d_rp, (n + 1) * sizeof(int)));
-        SYLV_CK(cudaMemcpy(d_rp, h.rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
-        if (!h.ci.empty()) {
-            SYLV_CK(cudaMalloc((void**)&d_ci, h.ci.size() * sizeof(int)));
-            SYLV_CK(cudaMalloc((void**)&d_v, h.v.size() * sizeof(double)));
-            SYLV_CK(cudaMemcpy(d_ci, h.ci.data(), h.ci.size() * sizeof(int), cudaMemcpyHostToDevice));
-            SYLV_CK(cudaMemcpy(d_v, h.v.data(), h.v.size() * sizeof(double), cudaMemcpyHostToDevice));
-        }
+        SYLV_TRY(to_device(&d_rp, h.rp));
+        SYLV_TRY(to_device(&d_ci, h.ci));
+        SYLV_TRY(to_device(&d_v, h.v));
         desc.rowptr = d_rp;
         desc.colind = d_ci;
         desc.val = d_v;
+        if (mass) {
+            SYLV_TRY(to_device(&d_mrp, mass->rp));
+            SYLV_TRY(to_device(&d_mci, mass->ci));
+            SYLV_TRY(to_device(&d_mv, mass->v));
+            desc.mrowptr = d_mrp;
+            desc.mcolind = d_mci;
+            desc.mvalc = d_mv;
+        }
     }
     is_stencil = stencil ? 1 : 0;
-    SYLV_CK(cudaMalloc((void**)&d_diag, n * sizeof(double)));
-    SYLV_CK(cudaMemcpy(d_diag, diag.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    SYLV_TRY(to_device(&d_diag, diag));
     desc.diag = d_diag;
+    if (mass) {
+        SYLV_TRY(to_device(&d_mdiag, mdiag));
+        desc.mdiag = d_mdiag;
+    }
     return SYLV_OK;
 }
 

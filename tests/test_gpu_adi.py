@@ -33,7 +33,8 @@ def run_gpu(p, **opts):
 def compare(p, strategy, jacobi, xtol=1e-6, **extra):
     st, info, hist, Z, Y, gam = run_gpu(p, strategy=strategy, jacobi=int(jacobi), **extra)
     ref = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy=strategy, jacobi=jacobi,
-                **{k: v for k, v in extra.items() if k in ("kmax", "xi", "fixed_tol", "max_inner", "restart", "ortho")})
+                **{k: v for k, v in extra.items() if k in ("kmax", "xi", "fixed_tol", "max_inner", "restart", "ortho",
+                                                           "inner")})
     A, B = p.A.to_scipy(), p.B.to_scipy()
     nfg = lowrank_norm2(p.f, p.g)
     assert st == 0, P.sylv_last_error()
