@@ -127,21 +127,23 @@ def shifted_apply(S, sigma, x, mass=None):
 
 
 def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
-          jacobi: bool = False, ortho: str = "cgs2", mass=None) -> GmresResult:
+          jacobi: bool = False, ortho: str = "cgs2", mass=None, x0=None) -> GmresResult:
     """GMRES(restart) for (S + sigma I) x = b, stop when ||b - (S+sigma I)x|| <= tol.
 
     S is a scipy sparse matrix, sigma a real or complex scalar; with a
     (sparse) mass matrix the system is (S + sigma Mass) x = b.  With
     jacobi=True the method runs on (S + sigma I) P^{-1} u = b with
     P = diag(S) + sigma I (diag(S) + sigma diag(Mass)) and returns x = P^{-1} u.
+    x0: initial guess (zero when None); the cycles then solve for the
+    correction from the residual b - (S + sigma I) x0.
     """
     dtype = np.result_type(S.dtype, np.asarray(sigma).dtype, b.dtype)
     n = b.shape[0]
     b = b.astype(dtype)
     dmass = 1.0 if mass is None else mass.diagonal().astype(dtype)
     pinv = 1.0 / (S.diagonal().astype(dtype) + sigma * dmass) if jacobi else np.ones(n, dtype)
-    x = np.zeros(n, dtype)
-    r = b.copy()
+    x = np.zeros(n, dtype) if x0 is None else np.asarray(x0, dtype).copy()
+    r = b.copy() if x0 is None else b - shifted_apply(S, sigma, x, mass)
     beta = np.linalg.norm(r)
     hist = []
     iters = cycles = 0
@@ -149,7 +151,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
         return GmresResult(x, beta, 0, 0, True, hist)
     m = restart
     if ortho == "dcgs2":
-        return _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass)
+        return _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass, x)
     while True:
         cycles += 1
         V = np.zeros((m + 1, n), dtype)
@@ -206,7 +208,7 @@ def gmres(S, sigma, b, tol: float, restart: int = 30, max_iters: int = 20000,
             return GmresResult(x, beta, iters, cycles, False, hist)
 
 
-def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None) -> GmresResult:
+def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None, x0=None) -> GmresResult:
     """The restarted GMRES above with the Arnoldi steps of arnoldi_dcgs2.
 
     Column j-1 of the Hessenberg matrix is complete once step j has the
@@ -214,8 +216,8 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None) -> Gmre
     test follow, so a cycle that stops there has already formed the product
     of step j (unused).  Arnoldi steps are counted as completed columns."""
     n = b.shape[0]
-    x = np.zeros(n, dtype)
-    r = b.copy()
+    x = np.zeros(n, dtype) if x0 is None else x0.copy()
+    r = b - shifted_apply(S, sigma, x, mass)
     beta0 = np.linalg.norm(r)
     hist = []
     iters = cycles = 0
@@ -280,7 +282,7 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None) -> Gmre
 
 
 def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = False,
-             mass=None) -> GmresResult:
+             mass=None, x0=None) -> GmresResult:
     """BiCGstab (van der Vorst, SIAM J. Sci. Stat. Comput. 13 (1992)) for
     (S + sigma I) x = b, or (S + sigma Mass) x = b, with right Jacobi
     preconditioning: the short-recurrence inner solver the paper uses for
@@ -296,8 +298,8 @@ def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = Fal
     b = b.astype(dtype)
     dmass = 1.0 if mass is None else mass.diagonal().astype(dtype)
     pinv = 1.0 / (S.diagonal().astype(dtype) + sigma * dmass) if jacobi else np.ones(n, dtype)
-    x = np.zeros(n, dtype)
-    r = b.copy()
+    x = np.zeros(n, dtype) if x0 is None else np.asarray(x0, dtype).copy()
+    r = b.copy() if x0 is None else b - shifted_apply(S, sigma, x, mass)
     rn = np.linalg.norm(r)
     hist = []
     iters = cycles = 0

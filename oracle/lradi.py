@@ -34,6 +34,9 @@ Readings where the paper is silent or inconsistent:
   skipped after the first member of a pair.
 * An inner solve that reaches its iteration cap keeps its best iterate and
   its achieved residual feeds u, v.
+* recycle="prev": each iterative inner solve starts from the multiple of
+  the previous step's solution (same side and column) with the smallest
+  residual (recycled_guess), a reading of the paper's outlook (Sec. 5).
 * Inner solvers: "direct" (sparse LU), "gmres" (restarted GMRES, right
   Jacobi) or "bicgstab" (the paper's short-recurrence choice, right Jacobi),
   for both sides (inner) or per side (inner_A, inner_B).  When exactly one
@@ -56,7 +59,7 @@ from .residual import block_norm2, lowrank_norm2
 DEFAULTS = dict(strategy="bl_mid", inner="gmres", inner_A=None, inner_B=None, restart=30, max_inner=20000,
                 jacobi=False, xi=1.0, dmin_A=None, dmin_B=None, dmax_A=0.1,
                 dmax_B=0.1, kmax=50, fixed_tol=None, ortho="cgs2",
-                keep_inner_residuals=False)
+                keep_inner_residuals=False, recycle=None)
 
 
 @dataclass
@@ -93,10 +96,21 @@ def _is_pair_start(alpha, beta, idx):
     return np.conj(a) == alpha[idx + 1] and np.conj(b) == beta[idx + 1]
 
 
-def _iterative(solver, S, sigma, b, tol, o, mass):
+def recycled_guess(S, sigma, b, u, mass=None):
+    """The multiple c u of the previous step's solution u with the smallest
+    residual ||b - c (S + sigma Mass) u||: c = (v^* b) / (v^* v), v the
+    shifted operator applied to u.  A reading of the paper's outlook (Sec. 5:
+    reuse what earlier shifted solves computed for the later ones); the
+    paper defines no such method.  Zero when u is zero."""
+    v = S @ u + sigma * (u if mass is None else mass @ u)
+    vv = np.vdot(v, v).real
+    return (np.vdot(v, b) / vv) * u if vv > 0.0 else np.zeros_like(u)
+
+
+def _iterative(solver, S, sigma, b, tol, o, mass, x0=None):
     if solver == "gmres":
-        return gmres(S, sigma, b, tol, o["restart"], o["max_inner"], o["jacobi"], o["ortho"], mass=mass)
-    return bicgstab(S, sigma, b, tol, o["max_inner"], o["jacobi"], mass=mass)
+        return gmres(S, sigma, b, tol, o["restart"], o["max_inner"], o["jacobi"], o["ortho"], mass=mass, x0=x0)
+    return bicgstab(S, sigma, b, tol, o["max_inner"], o["jacobi"], mass=mass, x0=x0)
 
 
 def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) -> LradiResult:
@@ -173,7 +187,10 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) ->
                     lu_cache[key] = spla.splu((SA + b_k * mA).astype(dt).tocsc())
                 z[:, l] = lu_cache[key].solve(w[:, l])
             else:
-                ra = _iterative(solver_A, SA, b_k, w[:, l], dA / r, o, SM)
+                x0 = None
+                if o["recycle"] == "prev" and Zs:
+                    x0 = recycled_guess(SA, b_k, w[:, l].astype(dt), Zs[-1][:, l].astype(dt), SM)
+                ra = _iterative(solver_A, SA, b_k, w[:, l], dA / r, o, SM, x0)
                 z[:, l] = ra.x
                 itsA += ra.iters
                 okA &= ra.converged
@@ -184,7 +201,10 @@ def lradi(A, B, f, g, alpha, beta, tau: float = 1e-8, M=None, C=None, **opts) ->
                     lu_cache[key] = spla.splu((SBt + np.conj(a_k) * mB).astype(dt).tocsc())
                 y[:, l] = lu_cache[key].solve(t[:, l])
             else:
-                rb = _iterative(solver_B, SBt, np.conj(a_k), t[:, l], dB / r, o, SCt)
+                x0 = None
+                if o["recycle"] == "prev" and Ys:
+                    x0 = recycled_guess(SBt, np.conj(a_k), t[:, l].astype(dt), Ys[-1][:, l].astype(dt), SCt)
+                rb = _iterative(solver_B, SBt, np.conj(a_k), t[:, l], dB / r, o, SCt, x0)
                 y[:, l] = rb.x
                 itsB += rb.iters
                 okB &= rb.converged

@@ -15,7 +15,7 @@ import scipy.sparse.linalg as spla
 from paper_2312_02891_gb300 import workloads as W
 from oracle import controller as ctl
 from oracle.dense import dense_residual, kron_solve
-from oracle.gmres import bicgstab
+from oracle.gmres import bicgstab, gmres, shifted_apply
 from oracle.lradi import lradi
 from oracle.residual import true_residual_norm2
 
@@ -152,3 +152,62 @@ def test_one_side_direct(small, iterative):
         u, v = h["u"], h["v"]
     A, B = p.A.to_scipy(), p.B.to_scipy()
     assert true_residual_norm2(A, B, p.f, p.g, dy.Z, dy.gamma, dy.Y) <= 3 * eps
+
+
+# ---------------------------------------------------------------- initial guesses
+
+def test_initial_guess_is_used_by_both_solvers():
+    """x0 = the exact solution: no step is taken and x0 is returned; a
+    nonzero x0 elsewhere still reaches the tolerance (the cycles solve for the
+    correction from b - (S + sigma I) x0)."""
+    p = W.problem_config("tiny2d")
+    S = p.A.to_scipy()
+    n = S.shape[0]
+    sigma = -40.0
+    b = np.random.default_rng(2).standard_normal(n)
+    xs = spla.spsolve((S + sigma * sp.identity(n)).tocsc(), b)
+    for solve in (lambda x0: gmres(S, sigma, b, 1e-10, 30, 500, True, "cgs2", x0=x0),
+                  lambda x0: gmres(S, sigma, b, 1e-10, 30, 500, True, "dcgs2", x0=x0),
+                  lambda x0: bicgstab(S, sigma, b, 1e-10, 500, True, x0=x0)):
+        r = solve(xs)
+        assert r.iters == 0 and np.array_equal(r.x, xs)
+        r = solve(0.5 * xs)
+        assert r.converged and np.linalg.norm(b - shifted_apply(S, sigma, r.x)) <= 1e-10
+
+
+def test_recycled_guess_minimises_the_residual_over_the_previous_solution():
+    """recycled_guess(c u): the residual b - c v (v = (S + sigma I) u) is
+    orthogonal to v, and no other multiple of u has a smaller residual."""
+    from oracle.lradi import recycled_guess
+    p = W.problem_config("tiny2d")
+    S = p.A.to_scipy()
+    n = S.shape[0]
+    rng = np.random.default_rng(5)
+    b, u = rng.standard_normal(n), rng.standard_normal(n)
+    sigma = -30.0 + 7.0j
+    x0 = recycled_guess(S, sigma, b.astype(complex), u.astype(complex))
+    v = shifted_apply(S, sigma, u.astype(complex))
+    res = b - shifted_apply(S, sigma, x0)
+    assert abs(np.vdot(v, res)) <= 1e-12 * np.linalg.norm(v) * np.linalg.norm(b)
+    c = np.vdot(v, b) / np.vdot(v, v)
+    for d in (1e-3, -1e-3, 1e-3j):
+        assert np.linalg.norm(b - (c + d) * v) > np.linalg.norm(res)
+    assert not recycled_guess(S, sigma, b, np.zeros(n)).any()
+
+
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+def test_recycled_initial_guesses_keep_the_solution(inner):
+    """With recycle="prev" the inner solves start from the recycled guess; the
+    outer steps and the solution are those of x0 = 0 (within the inexactness),
+    and with direct solves the option changes nothing."""
+    p = W.problem_config("small2d")
+    a = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy="nobl_mid", jacobi=True, inner=inner)
+    b = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy="nobl_mid", jacobi=True, inner=inner,
+              recycle="prev")
+    assert a.converged and b.converged and a.steps == b.steps
+    Xa = (a.Z * a.gamma[None, :]) @ a.Y.conj().T
+    Xb = (b.Z * b.gamma[None, :]) @ b.Y.conj().T
+    assert np.linalg.norm(Xa - Xb) <= 1e-6 * np.linalg.norm(Xa)
+    d1 = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, inner="direct", kmax=6)
+    d2 = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, inner="direct", kmax=6, recycle="prev")
+    assert np.array_equal(d1.Z, d2.Z) and np.array_equal(d1.Y, d2.Y)
