@@ -1,19 +1,24 @@
 #!/usr/bin/env python
 """Time to relative residual 1e-8 of the inexact LR-ADI Sylvester solver on GB300.
 
-One step = one full solve of Algorithm 1 (all inner shifted GMRES solves,
-factor updates, Gram residual norms, device controller) on the mid-size 2D
-convection-diffusion workload: A from N=512 (n = 262144, omega = 50 (x, y)),
-B from N=400 (m = 160000, omega = 20 (y, -x)), r = 2, 12 real shift pairs,
-right-Jacobi GMRES(30), "mid" tolerances without back-looking, tau = 1e-8,
-mixed precision (float32 Krylov basis and sweeps, float64 restart residuals,
-least squares, factors and outer iteration).  The line also carries the
-plain float64 run, the float64 run with a fixed inner tolerance of 1e-12,
-the bfloat16-basis run, the graph-driven runs and the batched workload (64
-independent instances in one device loop).
+Headline workload (default ``--workload batch64``): 64 independent 2D
+Sylvester instances A_i X + X B_i = -f_i g_i^* solved together by the batched
+solver - N_A, N_B ~ U{64..256} (n, m from 4096 to 65536), r ~ U{1, 2, 4},
+convection magnitudes ~ U[0, 50], 10 real shift pairs each, "mid" inner
+tolerances without back-looking, tau = 1e-8 - with BiCGstab inner solves in
+mixed precision (float32 vectors and products, float64 solutions, restart
+residuals and outer iteration) and one CUDA graph per solve.  One step = one
+solve of all 64 instances.  The working set (about 1 GB) exceeds the 129 MB
+L2, so the kernels' GB/s are HBM figures.
+
+The line also carries the comparisons the benchmark asks for - the plain
+float64 method, float64 with a fixed inner tolerance of 1e-12 (standing in
+for exact solves), GMRES inner solves - on the batch and on the single 2D
+workload (A: N = 512, B: N = 400, r = 2).  ``--workload mid2d|mid3d|large3d``
+times a single instance instead.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
-bounded samples of the same workload instead.
+a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -23,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -31,6 +37,10 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-rel.residual 1e-8 (s) and SpMM/orthog HBM GB/s, mixed+batched vs FP64"
 UNIT = "s"
 L2_FLUSH_BYTES = 512 << 20
+BATCH_COUNT = 64
+# instances of the batch that the CPU oracle solves in full for its baseline
+# (smallest first; the reference arm's step is the first of them)
+CPU_SAMPLE = (32, 4, 28, 0)
 
 
 def parse():
@@ -39,21 +49,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid2d")
+    ap.add_argument("--workload", default="batch64",
+                    help="batch64 (64 instances, the headline), or one instance: mid2d, mid3d, large3d, small2d")
     ap.add_argument("--strategy", default="nobl_mid")
+    ap.add_argument("--inner", default="bicgstab", choices=["gmres", "bicgstab"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"],
+                    help="fp32: float32 inner vectors/basis, float64 outer iteration")
+    ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"], help="GMRES orthogonalisation")
+    ap.add_argument("--real-pairs", type=int, default=1, help="real double steps for complex shift pairs")
+    ap.add_argument("--kmax", type=int, default=50, help="outer step cap (small values give short profiler cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload among the variants")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"],
-                    help="precision of the headline solve (the benchmark line uses fp32: float32 "
-                         "Krylov basis and sweeps, float64 outer iteration)")
-    ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"],
-                    help="Arnoldi orthogonalisation of the inner GMRES (all runs of the line)")
-    ap.add_argument("--inner", default="gmres", choices=["gmres", "bicgstab"],
-                    help="inner solver of the headline solve")
-    ap.add_argument("--kmax", type=int, default=50,
-                    help="outer step cap (a small value gives a short case for profilers)")
-    ap.add_argument("--cpu-sample-its", type=int, default=60)
+    ap.add_argument("--clock-log", default=os.path.join(tempfile.gettempdir(), "sylv_clocks_rank{rank}.csv"),
+                    help="where the nvidia-smi clock samples of the timed region are written")
+    ap.add_argument("--gen-workers", type=int, default=min(16, os.cpu_count() or 1),
+                    help="processes generating the batch instances")
     return ap.parse_args()
 
 
@@ -83,13 +93,15 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = path
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        d = os.path.dirname(self.path)
+        if d:
+            os.makedirs(d, exist_ok=True)
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -130,140 +142,210 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
+# The oracle (plain numpy / scipy float64, test infrastructure) runs in a
+# fresh interpreter with one BLAS thread; its output is only timed.
 
-def cpu_sample(workload: str, its: int, threads: int = 1):
-    """Oracle GMRES on the first outer step's A and B systems, `its` Arnoldi
-    steps each (whole restart cycles), timed on this host; run in a fresh
-    interpreter with `threads` BLAS / OpenMP threads (the sparse products of
-    the oracle are single-threaded; its dense basis operations use them)."""
-    code = f"""
-import json, time, numpy as np, sys
+def _oracle_script(body: str) -> str:
+    return f"""
+import json, sys, time
 sys.path.insert(0, {ROOT!r})
+import numpy as np
 from paper_2312_02891_gb300 import workloads as W
-from oracle.gmres import gmres
-p = W.problem_config({workload!r})
-S = p.A.to_scipy(); Bt = p.B.to_scipy().T.tocsr()
-jac = bool(p.opts.get('jacobi', False)); m = p.opts.get('restart', 30)
-out = {{}}
-for side, M, sig, b in (('A', S, p.beta[0], p.f[:, 0]), ('B', Bt, np.conj(p.alpha[0]), p.g[:, 0])):
-    t = time.perf_counter()
-    r = gmres(M, sig, b, 1e-300, m, {its}, jac, 'cgs2')
-    out[side] = (time.perf_counter() - t) / r.iters
-print(json.dumps(out))
+from oracle.lradi import lradi
+{body}
 """
-    nt = str(int(threads))
-    env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt)
-    t0 = time.perf_counter()
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+
+
+def run_oracle(body: str) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", _oracle_script(body)], capture_output=True, text=True, env=env)
     if p.returncode != 0:
-        raise RuntimeError(p.stderr)
-    per_it = json.loads(p.stdout.strip().splitlines()[-1])
-    return per_it, time.perf_counter() - t0
+        raise RuntimeError(p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def golden(workload: str, strategy: str):
-    path = os.path.join(ROOT, "tests", "golden", f"{workload}_{strategy}.json")
-    if os.path.exists(path):
-        with open(path) as fh:
-            return json.load(fh)
-    return None
+def oracle_batch_instances(indices, strategy, inner) -> dict:
+    """Full oracle solves of the given batch instances: per instance the
+    seconds of the solve (generation excluded), its rows x rank and its outer
+    steps."""
+    return run_oracle(f"""
+out = {{}}
+for i in {list(indices)!r}:
+    p = W.batch_problems(1, base_seed=1000 + i)[0]
+    t = time.perf_counter()
+    r = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy={strategy!r}, jacobi=True, inner={inner!r})
+    out[i] = [time.perf_counter() - t, (p.A.n + p.B.n) * p.r, r.steps, bool(r.converged)]
+print(json.dumps(out))
+""")
 
 
-def cpu_baseline(workload, strategy, its, gpu_info=None, threads: int = 1):
-    per_it, wall = cpu_sample(workload, its, threads)
-    g = golden(workload, strategy)
-    if g is not None:
-        itsA, itsB, src = g["inner_its_A"], g["inner_its_B"], "stored oracle run"
-    else:
-        itsA, itsB, src = gpu_info["inner_its_A"], gpu_info["inner_its_B"], "this GPU run"
-    est = itsA * per_it["A"] + itsB * per_it["B"]
-    return {"value": est, "unit": UNIT, "cores": int(threads), "kind": "oracle",
-            "sample": (f"oracle GMRES(30) on step-1 A and B systems, {its} Arnoldi steps each, "
-                       f"{per_it['A'] * 1e3:.2f} / {per_it['B'] * 1e3:.2f} ms per step (A/B), "
-                       f"scaled by the inner-step totals of the {src} "
-                       f"({itsA} A + {itsB} B); sample wall {wall:.1f} s")}
+def oracle_single(workload, strategy, inner) -> dict:
+    return run_oracle(f"""
+p = W.problem_config({workload!r})
+t = time.perf_counter()
+r = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy={strategy!r},
+          jacobi=bool(p.opts.get('jacobi', False)), inner={inner!r})
+print(json.dumps({{"s": time.perf_counter() - t, "steps": r.steps, "converged": bool(r.converged)}}))
+""")
+
+
+def batch_rows(probs) -> int:
+    return sum((p.A.n + p.B.n) * p.r for p in probs)
+
+
+def cpu_baseline_batch(probs, strategy, inner) -> dict:
+    """Full oracle solves of four batch instances (about 10 s on one core),
+    scaled to the 64-instance batch by rows x rank; one full oracle solve of
+    the smallest 2D workload (n = 1024, m = 900) as a measured anchor."""
+    res = oracle_batch_instances(CPU_SAMPLE, strategy, inner)
+    ts = sum(v[0] for v in res.values())
+    rs = sum(v[1] for v in res.values())
+    est = ts * batch_rows(probs) / rs
+    anchor = oracle_single("small2d", strategy, "gmres")
+    return {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"full oracle solves ({inner} inner, float64, one thread) of batch instances "
+                       f"{list(CPU_SAMPLE)}: {ts:.1f} s for {rs} rows x rank, scaled by rows x rank to the "
+                       f"{batch_rows(probs)} of the batch"),
+            "instances": {str(k): {"s": round(v[0], 3), "rows_x_r": v[1], "steps": v[2]} for k, v in res.items()},
+            "anchor_small2d_full_solve_s": round(anchor["s"], 3)}
 
 
 # ------------------------------------------------------------------- main
 
 def run_reference(a):
+    """The oracle as it stands, one core, on the benchmark workload: each step
+    is one full solve of the smallest instance of the batch (a bounded
+    sample), timed as it runs; the scaled estimate of the whole batch is
+    reported beside it."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    vals = []
-    for s in range(a.warmup + a.steps):
-        cb = cpu_baseline(a.workload, a.strategy, a.cpu_sample_its)
-        if s >= a.warmup:
-            vals.append(cb["value"])
-    v = statistics.mean(vals)
+    if a.workload != "batch64":
+        steps = []
+        for s in range(a.warmup + a.steps):
+            r = oracle_single(a.workload, a.strategy, a.inner)
+            if s >= a.warmup:
+                steps.append(r["s"])
+        v = statistics.mean(steps)
+        sample = f"full oracle solve of {a.workload} ({a.inner} inner, float64, one thread)"
+        extra = {}
+    else:
+        i0 = CPU_SAMPLE[0]
+        steps, rows0 = [], None
+        for s in range(a.warmup + a.steps):
+            res = oracle_batch_instances([i0], a.strategy, a.inner)
+            t, rows0 = res[str(i0)][0], res[str(i0)][1]
+            if s >= a.warmup:
+                steps.append(t)
+        v = statistics.mean(steps)
+        total = sum((p.A.n + p.B.n) * p.r for p in [_instance_sizes(i) for i in range(BATCH_COUNT)])
+        sample = (f"full oracle solve ({a.inner} inner, float64, one thread) of batch instance {i0} "
+                  f"({rows0} rows x rank) per step")
+        extra = {"extrapolated_batch64_s": v * total / rows0,
+                 "extrapolation": f"per step time x {total} / {rows0} (rows x rank of the batch / of the sample)"}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": a.workload, "strategy": a.strategy},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v,
-                             "unit": UNIT},
+            "config": {"workload": a.workload, "strategy": a.strategy, "inner": a.inner},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v, "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
 
 
+class _Sizes:
+    def __init__(self, n, m, r):
+        self.A, self.B, self.r = type("O", (), {"n": n})(), type("O", (), {"n": m})(), r
+
+
+def _instance_sizes(i: int):
+    """Sizes of batch instance i without building it (the seeded size draw of
+    workloads.batch_problems)."""
+    from paper_2312_02891_gb300 import workloads as W
+    u = W._uniform53(1000 + i, 9, 0, 0, 5)
+    NA = 64 + int(u[0] * 193)
+    NB = 64 + int(u[1] * 193)
+    return _Sizes(NA * NA, NB * NB, (1, 2, 4)[int(u[2] * 3)])
+
+
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 float64 rate (nominal, dense)
-SWEEPS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
-# with the delayed CGS2 the first and third counters hold its two kernels
-DCGS2_NAMES = {"arnoldi_spmv": "k_dcgs_a (product + all dots)", "cgs_pass3": "k_dcgs_b (basis update)"}
-# DRAM traffic / algorithmic bytes of the sweep kernels from one ncu capture
-# of the current kernels (None once a kernel changes after its capture)
+KNAMES = {
+    "bicgstab": {"arnoldi_spmv": "k_bicg_a (p update + product + rhat^* v)",
+                 "cgs_pass2": "k_bicg_b (product + t^* s, t^* t, s^* s)",
+                 "cgs_pass3": "k_bicg_c (x, r, q updates + rhat^* r, r^* r)",
+                 "restart_residual": "k_bicg_resid (float64 true residual)"},
+    "dcgs2": {"arnoldi_spmv": "k_dcgs_a (product + all dots)", "cgs_pass3": "k_dcgs_b (basis update)"},
+    "cgs2": {},
+}
+INNER_KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
+# DRAM traffic / algorithmic bytes of a kernel from one ncu capture of the
+# current kernels on the same workload, keyed by (inner solver, kernel); a
+# kernel changed after its capture has no entry (traffic null)
 NCU_TRAFFIC_RATIO = {}
+
+
+def kernel_table(stats, names):
+    total_ms = sum(v[0] for v in stats.values())
+    return {names.get(k, k): {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
+                              "launches": v[3],
+                              "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None,
+                              "TFLOPs": round(v[2] / (v[0] * 1e-3) / 1e12, 4) if v[0] > 0 else None}
+            for k, v in stats.items() if v[3] > 0}
+
+
+def roofline_of(stats, names, hbm, hbm_src, inner):
+    dom = max(INNER_KERNELS, key=lambda k: stats[k][0])
+    ms, by, fl, la = stats[dom]
+    ach = (by / la) / ((ms / la) * 1e-3) / 1e9 if ms > 0 else None
+    ratio = NCU_TRAFFIC_RATIO.get((inner, dom))
+    inner_ms = sum(stats[k][0] for k in INNER_KERNELS + ("restart_update", "restart_residual"))
+    inner_by = sum(stats[k][1] for k in INNER_KERNELS + ("restart_update", "restart_residual"))
+    return {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": (ach / hbm) if ach else None, "peak_source": hbm_src,
+            "traffic": (ratio * by / la) if ratio else None,
+            "algorithmic_bytes_per_launch": by / la if la else None,
+            "inner_kernels_GBps": inner_by / (inner_ms * 1e-3) / 1e9 if inner_ms else None,
+            "inner_kernels_frac": (inner_by / (inner_ms * 1e-3) / 1e9 / hbm) if inner_ms else None}
 
 
 def run_ours(a):
     import ctypes as C
 
     import numpy as np
-    import torch
 
-    import paper_2312_02891_gb300 as P
     from paper_2312_02891_gb300 import workloads as W
 
     ws, rank, local = dist_env()
+    batch = a.workload == "batch64"
+    # the batch instances are generated in spawned processes before the first
+    # GPU call (a process forked after it could hang)
+    probs = W.batch_problems(BATCH_COUNT, workers=a.gen_workers) if (batch or not a.no_variants) else []
+    p2d = W.problem_config("mid2d") if (not batch or not a.no_variants) else None
+    single = None if batch else (p2d if a.workload == "mid2d" else W.problem_config(a.workload))
+
+    import torch
+    import paper_2312_02891_gb300 as P
+
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    p = W.problem_config(a.workload)
-    # the 64 batched instances are generated on a host thread meanwhile
-    # (shift selection runs sparse LU solves; the solver calls release the GIL)
-    from concurrent.futures import ThreadPoolExecutor
-    pool = ThreadPoolExecutor(max_workers=1)
-    batch_future = None if (a.no_variants or a.no_batch) else pool.submit(W.batch_problems, 64)
     stream = torch.cuda.Stream()
-    jac = int(p.opts.get("jacobi", False))
-    rst = p.opts.get("restart", 30)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    n, m, r = p.A.n, p.B.n, p.r
 
     def barrier():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
 
-    def make(**kw):
-        kw.setdefault("kmax", a.kmax)
-        kw.setdefault("ortho", a.ortho)
-        kw.setdefault("inner", a.inner)
-        return P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, stream=stream,
-                              jacobi=jac, restart=rst, **kw)
-
-    def timed(solver, warmup, steps, profile=False):
+    def timed(solver, warmup, steps):
         """Mean device seconds per solve (CUDA events on the solver stream),
         L2 flushed before every timed solve."""
         for _ in range(warmup):
             solver.solve()
-        if profile:
-            solver.profile(True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         st = 0
         for k in range(steps):
@@ -274,32 +356,38 @@ def run_ours(a):
             with torch.cuda.stream(stream):
                 ev[k][1].record(stream)
         barrier()
-        solver.timed_solves = steps
         t = sum(s.elapsed_time(e) for s, e in ev) / 1e3 / steps
         return max_over_ranks(t, "cuda"), st
 
-    def summary(solver, t, st):
-        info = solver.info()
-        stats = solver.kernel_stats()
-        so_ms = sum(stats[k][0] for k in SWEEPS)
-        so_by = sum(stats[k][1] for k in SWEEPS)
+    def make_batch(**kw):
+        o = dict(strategy=a.strategy, precision=a.precision, jacobi=1, restart=30, inner=a.inner,
+                 ortho="cgs2" if a.inner == "bicgstab" else a.ortho, kmax=a.kmax, autotune=1)
+        o.update(kw)
+        return P.SylvesterADIBatch(probs, stream=stream, **o)
+
+    def make_single(p, **kw):
+        o = dict(strategy=a.strategy, precision=a.precision, jacobi=int(p.opts.get("jacobi", False)),
+                 restart=p.opts.get("restart", 30), inner=a.inner, ortho=a.ortho, kmax=a.kmax, autotune=1)
+        if np.iscomplexobj(p.alpha) or np.iscomplexobj(p.beta):
+            o["real_pairs"] = a.real_pairs
+        o.update(kw)
+        return P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, stream=stream, **o)
+
+    def batch_summary(bt, t, st, nsolve):
+        infos = [bt.info(i) for i in range(len(probs))]
+        bs = bt.stats()
+        return {"s": t, "instances_per_s": len(probs) / t, "status": st,
+                "converged": sum(1 for q, i_ in zip(probs, infos) if i_["status"] == 0 and i_["rel_res_comp"] < q.tau),
+                "outer_steps_total": sum(i_["steps"] for i_ in infos),
+                "inner_its_total": sum(i_["inner_its_A"] + i_["inner_its_B"] for i_ in infos),
+                "ticks_per_solve": bs["ticks"], "launches_per_solve": bs["launches"],
+                "algorithmic_GBps": bs["bytes"] / nsolve / t / 1e9}, infos
+
+    def single_summary(sv, t, st):
+        info = sv.info()
         return {"s": t, "status": st, "outer_steps": info["steps"], "inner_its_A": info["inner_its_A"],
                 "inner_its_B": info["inner_its_B"], "rel_res_comp": info["rel_res_comp"],
-                "launches_per_solve": info["launches"], "ticks_per_solve": info["ticks"],
-                "spmm_orth_GBps": so_by / (so_ms * 1e-3) / 1e9 if so_ms else None,
-                "kernel_ms_per_solve": {k: round(v[0] / max(1, solver.timed_solves), 2)
-                                        for k, v in stats.items() if v[3] > 0}}, info, stats
-
-    def kname(k):
-        return DCGS2_NAMES.get(k, k) if a.ortho == "dcgs2" else k
-
-    def kernel_table(stats):
-        total_ms = sum(v[0] for v in stats.values())
-        return {kname(k): {"ms": round(v[0], 3), "share": round(v[0] / total_ms, 4) if total_ms else None,
-                    "launches": v[3],
-                    "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] > 0 else None,
-                    "TFLOPs": round(v[2] / (v[0] * 1e-3) / 1e12, 4) if v[0] > 0 else None}
-                for k, v in stats.items() if v[3] > 0}
+                "launches_per_solve": info["launches"]}, info
 
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -309,161 +397,161 @@ def run_ours(a):
     hbm = peaks.get("hbm_gbs")
     hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs, copy kernel)" if hbm else "fallback 6800 GB/s"
     hbm = hbm or 6800.0
+    names = KNAMES["bicgstab" if a.inner == "bicgstab" else a.ortho]
+    sampler = ClockSampler(local, a.clock_log.format(rank=rank))
 
-    # ---- headline: mixed precision (float32 Krylov basis and sweeps, float64
-    # outer iteration), adaptive inner tolerances; host driver with CUDA
-    # events on every 4th device iteration for the per-kernel times ----
+    # ---------------- headline ----------------
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    solver = make(strategy=a.strategy, precision=a.precision, driver=1)
+    if batch:
+        head = make_batch()
+        n_items = len(probs)
+    else:
+        head = make_single(single)
+        n_items = 1
     torch.cuda.synchronize()
     footprint = free0 - torch.cuda.mem_get_info()[0]
-    sampler = ClockSampler(local)
+    tuning = head.tuning()
     sampler.start()
     time.sleep(0.3)
-    t_solve, st = timed(solver, a.warmup, a.steps, profile=True)
+    nsolve0 = a.warmup + a.steps
+    t_solve, st = timed(head, a.warmup, a.steps)
     clocks = sampler.stop()
-    main_sum, info, stats = summary(solver, t_solve, st)
-    solver.profile(False)
+    if batch:
+        main_sum, infos = batch_summary(head, t_solve, st, nsolve0)
+        launches = main_sum["launches_per_solve"]
+    else:
+        main_sum, info = single_summary(head, t_solve, st)
+        launches = info["launches"]
 
-    # ---- end to end through the public API with host buffers ----
-    fh = torch.from_numpy(np.asfortranarray(p.f)).pin_memory()
-    gh = torch.from_numpy(np.asfortranarray(p.g)).pin_memory()
-    kr = info["kr"]
-    fdt = torch.complex128 if info["is_complex"] else torch.float64
-    Zh = torch.empty((kr, n), dtype=fdt).pin_memory()
-    Yh = torch.empty((kr, m), dtype=fdt).pin_memory()
-    gmh = torch.empty(kr, dtype=fdt).pin_memory()
-    e2e = []
-    for k in range(a.steps):
-        flush.zero_()
-        barrier()
-        t0 = time.perf_counter()
-        P.sylv_adi_set_rhs(solver.h, fh.numpy(), gh.numpy())
-        solver.solve()
-        kro, isc = C.c_int32(), C.c_int32()
-        P.load().sylv_adi_factors(solver.h, Zh.data_ptr(), Yh.data_ptr(), gmh.data_ptr(), 0,
-                                  C.byref(kro), C.byref(isc))
-        e2e.append(time.perf_counter() - t0)
+    # per-kernel CUDA events: one more solve, host-driven, every fourth
+    # device iteration's kernels bracketed by events
+    if batch:
+        prof = make_batch(driver=1)
+    else:
+        prof = make_single(single, driver=1)
+    prof.solve()
+    prof.profile(True)
+    prof.solve()
+    stats = prof.kernel_stats()
+    prof.profile(False)
+    prof.close()
+    roof = roofline_of(stats, names, hbm, hbm_src, a.inner)
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    e2e_steps = max(1, min(a.steps, 3))
+    if batch:
+        fh = [torch.from_numpy(np.asfortranarray(q.f)).pin_memory() for q in probs]
+        gh = [torch.from_numpy(np.asfortranarray(q.g)).pin_memory() for q in probs]
+        outs = []
+        for q, i_ in zip(probs, infos):
+            kr = i_["kr"]
+            outs.append((torch.empty((kr, q.A.n), dtype=torch.float64).pin_memory(),
+                         torch.empty((kr, q.B.n), dtype=torch.float64).pin_memory(),
+                         torch.empty(kr, dtype=torch.float64).pin_memory()))
+        h2d = sum(f.numel() + g.numel() for f, g in zip(fh, gh)) * 8
+        d2h = sum(z.numel() + y.numel() + g.numel() for z, y, g in outs) * 8
+        lib = P.load()
+        e2e = []
+        for _ in range(e2e_steps):
+            flush.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            for i in range(len(probs)):
+                P.sylv_adi_batch_set_rhs(head.h, i, fh[i].numpy(), gh[i].numpy())
+            head.solve()
+            kro, isc = C.c_int32(), C.c_int32()
+            for i, (z, y, g) in enumerate(outs):
+                lib.sylv_adi_batch_factors(head.h, i, z.data_ptr(), y.data_ptr(), g.data_ptr(), 0,
+                                           C.byref(kro), C.byref(isc))
+            e2e.append(time.perf_counter() - t0)
+    else:
+        fh = torch.from_numpy(np.asfortranarray(single.f)).pin_memory()
+        gh = torch.from_numpy(np.asfortranarray(single.g)).pin_memory()
+        kr = info["kr"]
+        real = info["is_complex"] == 0
+        fdt = torch.float64 if real else torch.complex128
+        Zh = torch.empty((kr, single.A.n), dtype=fdt).pin_memory()
+        Yh = torch.empty((kr, single.B.n), dtype=fdt).pin_memory()
+        gmh = torch.empty(kr, dtype=fdt).pin_memory()
+        h2d = (single.A.n + single.B.n) * single.r * 8
+        d2h = (Zh.numel() + Yh.numel() + gmh.numel()) * Zh.element_size()
+        e2e = []
+        for _ in range(e2e_steps):
+            flush.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            P.sylv_adi_set_rhs(head.h, fh.numpy(), gh.numpy())
+            head.solve()
+            kro, isc = C.c_int32(), C.c_int32()
+            P.load().sylv_adi_factors(head.h, Zh.data_ptr(), Yh.data_ptr(),
+                                      None if head.opts.real_pairs else gmh.data_ptr(), 0, C.byref(kro),
+                                      C.byref(isc))
+            e2e.append(time.perf_counter() - t0)
     barrier()
     e2e_v = max_over_ranks(sum(e2e) / len(e2e), "cuda")
-    solver.close()
+    head.close()
 
-    # ---- comparison runs ----
+    # ---------------- comparisons ----------------
     variants = {}
     if not a.no_variants:
-        for name, kw, w_, k_, prof in (
-                ("fp64", dict(strategy=a.strategy, precision="fp64"), 1, 2, True),
-                ("fp64_fixed_1e-12", dict(strategy="fixed", fixed_tol=1e-12, precision="fp64"), 0, 1, True),
-                ("bf16_basis", dict(strategy=a.strategy, precision="bf16"), 1, 2, True),
-                # one CUDA graph per solve, device-set conditional nodes (no kernel events)
-                ("fp32_graph", dict(strategy=a.strategy, precision="fp32", driver=0), 1, 3, False),
-                ("fp64_graph", dict(strategy=a.strategy, precision="fp64", driver=0), 1, 2, False),
-                ("fp32_cgs2", dict(strategy=a.strategy, precision="fp32", ortho="cgs2"), 1, 2, True),
-                ("fp32_bicgstab", dict(strategy=a.strategy, precision="fp32", inner="bicgstab"), 1, 3, True),
-                ("fp64_bicgstab", dict(strategy=a.strategy, precision="fp64", inner="bicgstab"), 1, 2, True),
-                ("fp32_bicgstab_graph", dict(strategy=a.strategy, precision="fp32", inner="bicgstab", driver=0),
-                 1, 3, False)):
-            sv = make(**kw)
-            tv, stv = timed(sv, w_, k_, profile=prof)
-            variants[name], _, vst = summary(sv, tv, stv)
-            variants[name]["strategy"] = kw["strategy"]
-            if name == "fp64":
-                # the float64 sweeps are bound by the float64 pipe
-                dk = max(SWEEPS, key=lambda k_: vst[k_][0])
-                ms_, by_, fl_, la_ = vst[dk]
-                tf = (fl_ / la_) / ((ms_ / la_) * 1e-3) / 1e12
-                variants[name]["roofline"] = {"bound": "alu", "kernel": dk, "achieved": tf,
-                                              "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                              "frac": tf / FP64_NOMINAL_TFLOPS}
-            sv.close()
-        fixed = variants["fp64_fixed_1e-12"]["s"]
-        variants["speedup_mixed_adaptive_vs_fp64_fixed_1e-12"] = fixed / t_solve
-        variants["speedup_mixed_adaptive_graph_vs_fp64_fixed_1e-12"] = fixed / variants["fp32_graph"]["s"]
-        variants["speedup_fp64_adaptive_vs_fp64_fixed_1e-12"] = fixed / variants["fp64"]["s"]
+        if probs:
+            for name, kw, w_, k_ in (
+                    ("batch64_fp64", dict(precision="fp64"), 1, 1),
+                    ("batch64_fp64_fixed_1e-12", dict(precision="fp64", strategy="fixed", fixed_tol=1e-12), 0, 1),
+                    ("batch64_fp32_gmres_cgs2", dict(inner="gmres", ortho="cgs2"), 1, 1),
+                    ("batch64_fp32_gmres_dcgs2", dict(inner="gmres", ortho="dcgs2"), 0, 1)):
+                with make_batch(**kw) as bt:
+                    tv, stv = timed(bt, w_, k_)
+                    variants[name], _ = batch_summary(bt, tv, stv, w_ + k_)
+            if batch:
+                f = variants["batch64_fp64_fixed_1e-12"]["s"]
+                variants["speedup_vs_fp64_fixed_1e-12"] = f / t_solve
+                variants["speedup_vs_fp64_adaptive"] = variants["batch64_fp64"]["s"] / t_solve
+                variants["speedup_vs_fp32_gmres_cgs2"] = variants["batch64_fp32_gmres_cgs2"]["s"] / t_solve
+        if p2d is not None:
+            for name, kw, w_, k_ in (
+                    ("mid2d_fp32_bicgstab", dict(inner="bicgstab"), 1, 2),
+                    ("mid2d_fp64_bicgstab", dict(inner="bicgstab", precision="fp64"), 1, 1),
+                    ("mid2d_fp32_gmres_dcgs2", dict(inner="gmres", ortho="dcgs2", driver=1), 1, 2),
+                    ("mid2d_fp64_gmres_dcgs2", dict(inner="gmres", ortho="dcgs2", precision="fp64"), 1, 1),
+                    ("mid2d_fp64_fixed_1e-12", dict(inner="gmres", ortho="dcgs2", precision="fp64",
+                                                    strategy="fixed", fixed_tol=1e-12), 0, 1)):
+                with make_single(p2d, **kw) as sv:
+                    tv, stv = timed(sv, w_, k_)
+                    variants[name], _ = single_summary(sv, tv, stv)
+            variants["mid2d_note"] = ("2D workload, one instance (A: N = 512, B: N = 400, r = 2): its working "
+                                      "set stays in L2, so its kernel rates are not HBM figures")
 
-        # ---- batched workload: 64 independent 2D instances in one device loop ----
-        probs = batch_future.result() if batch_future is not None else []
-        for prec, orth in ((("fp32", "cgs2"), ("fp32", "dcgs2"), ("fp64", "cgs2"), ("fp32", "bicgstab"))
-                           if probs else ()):
-            inner = "bicgstab" if orth == "bicgstab" else "gmres"
-            with P.SylvesterADIBatch(probs, stream=stream, strategy=a.strategy, precision=prec, jacobi=1,
-                                     restart=30, ortho="cgs2" if inner == "bicgstab" else orth,
-                                     inner=inner) as bt:
-                nsolve = 0
-                bt.solve()
-                nsolve += 1
-                evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                       for _ in range(2)]
-                barrier()
-                stb = 0
-                for k in range(2):
-                    with torch.cuda.stream(stream):
-                        flush.zero_()
-                        evb[k][0].record(stream)
-                    stb = bt.solve()
-                    nsolve += 1
-                    with torch.cuda.stream(stream):
-                        evb[k][1].record(stream)
-                barrier()
-                tb = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in evb) / 1e3 / 2, "cuda")
-                infos = [bt.info(i) for i in range(len(probs))]
-                bs = bt.stats()
-                variants[f"batch64_{prec}_{orth}"] = {
-                    "s": tb, "instances_per_s": len(probs) / tb, "status": stb,
-                    "converged": sum(1 for q, i_ in zip(probs, infos) if i_["status"] == 0 and i_["rel_res_comp"] < q.tau),
-                    "outer_steps_total": sum(i_["steps"] for i_ in infos),
-                    "inner_its_total": sum(i_["inner_its_A"] + i_["inner_its_B"] for i_ in infos),
-                    "ticks_per_solve": bs["ticks"], "launches_per_solve": bs["launches"],
-                    "algorithmic_GBps": bs["bytes"] / nsolve / tb / 1e9,
-                    "rows": sum((q.A.n + q.B.n) * q.r for q in probs)}
-    pool.shutdown()
-
-    # ---- roofline of the dominant kernel of the headline solve (HBM) ----
-    dom = max(SWEEPS, key=lambda k: stats[k][0])
-    ms, by, fl, la = stats[dom]
-    ach_gb = (by / la) / ((ms / la) * 1e-3) / 1e9 if ms > 0 else None
-    ratio = NCU_TRAFFIC_RATIO.get(dom)
-    # time lower bound of a solve: all its algorithmic bytes (every kernel,
-    # every launch of the timed solves) at the measured copy bandwidth
-    solve_bytes = sum(v[1] for v in stats.values()) / max(1, a.steps)
-    bound_s = solve_bytes / (hbm * 1e9)
     line = {
         "metric": METRIC, "value": t_solve, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 Krylov basis/sweeps + f64 outer" if a.precision == "fp32" else a.precision,
+        "dtype": ("f32 inner vectors + f64 outer" if a.precision == "fp32" else a.precision),
         "data": "synthetic",
-        "config": {"workload": a.workload, "n": n, "m": m, "r": r, "restart": rst,
-                   "jacobi": bool(jac), "strategy": a.strategy, "tau": p.tau, "precision": a.precision,
-                   "kmax": a.kmax, "ortho": a.ortho,
-                   "driver": "host (per-kernel CUDA events on every 4th device iteration)",
-                   "shifts": len(p.alpha), "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "flushed (512 MiB write) before every timed solve",
-                   "outer_steps": info["steps"], "inner_its_A": info["inner_its_A"],
-                   "inner_its_B": info["inner_its_B"], "rel_res_comp": info["rel_res_comp"],
-                   "status": st, "device_bytes_of_solver": footprint},
-        "roofline": {"bound": "hbm", "kernel": kname(dom), "achieved": ach_gb, "peak": hbm, "unit": "GB/s",
-                     "frac": (ach_gb / hbm) if ach_gb else None, "peak_source": hbm_src,
-                     "traffic": (ratio * by / la) if ratio else None,
-                     "sweeps_GBps": main_sum["spmm_orth_GBps"],
-                     "sweeps_frac": (main_sum["spmm_orth_GBps"] / hbm) if main_sum["spmm_orth_GBps"] else None,
-                     "solve_algorithmic_bytes": solve_bytes, "solve_time_lower_bound_s": bound_s,
-                     "solve_time_over_bound": (t_solve / bound_s) if bound_s > 0 else None},
-        "kernels": kernel_table(stats),
+        "config": ({"workload": "batch64", "instances": len(probs), "n_range": [min(q.A.n for q in probs),
+                                                                               max(q.A.n for q in probs)],
+                    "m_range": [min(q.B.n for q in probs), max(q.B.n for q in probs)],
+                    "r": sorted({q.r for q in probs}), "rows_x_r": batch_rows(probs)}
+                   if batch else {"workload": a.workload, "n": single.A.n, "m": single.B.n, "r": single.r}),
+        "roofline": roof,
+        "autotune": {"rows_per_chunk": tuning["rows_per_chunk"],
+                     "ms_per_device_iteration": {str(k): round(v, 4) for k, v in tuning["candidates"].items()}},
+        "kernels": kernel_table(stats, names),
         "variants": variants,
-        "gpu_launches": info["launches"] * a.steps,
+        "gpu_launches": int(launches) * a.steps,
         "clocks": clocks,
-        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": (n + m) * r * 8,
-                "d2h_bytes_per_step": ((n + m) * kr + kr) * (16 if info["is_complex"] else 8)},
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": e2e_steps},
     }
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a.workload, a.strategy, a.cpu_sample_its, info)
-        # the same oracle with every host core available to its dense operations
-        ncores = os.cpu_count() or 1
-        if ncores > 1:
-            allc = cpu_baseline(a.workload, a.strategy, a.cpu_sample_its, info, threads=ncores)
-            line["cpu_baseline"]["all_cores"] = {k: allc[k] for k in ("value", "unit", "cores", "sample")}
+    line["config"].update({"inner": a.inner, "precision": a.precision, "strategy": a.strategy, "tau": 1e-8,
+                           "kmax": a.kmax, "driver": "graph (one CUDA graph per solve)" if batch else "host",
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "flushed (512 MiB write) before every timed solve",
+                           "device_bytes_of_solver": footprint})
+    line["config"].update({k: v for k, v in main_sum.items() if k not in ("s",)})
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline and batch:
+        line["cpu_baseline"] = cpu_baseline_batch(probs, a.strategy, a.inner)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

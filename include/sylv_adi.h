@@ -134,6 +134,13 @@ typedef struct sylv_opts {
                                     side whose shift is real, real factors Z, Y and a real core
                                     with 2 x 2 blocks (sylv_adi_core).  Runs the host-driven loop;
                                     not built for batches with complex shifts. */
+    int32_t autotune;            /* with rows_per_chunk = 0: 1 times a bounded set of work-chunk
+                                    sizes (the one-wave rule and 512 .. 8192 rows) on the actual
+                                    systems at create - synthetic vectors and a stencil of the
+                                    operators' shape, CUDA events over a few device iterations -
+                                    and keeps the fastest (sylv_adi_tuning reports them); 0 (the
+                                    default) uses the one-wave rule, so that results do not
+                                    depend on timing */
 } sylv_opts;
 
 #define SYLV_INNER_GMRES     0
@@ -362,6 +369,13 @@ int sylv_adi_destroy(sylv_handle* h);
  * Z, Y and must be given gamma = NULL. */
 int sylv_adi_core(const sylv_handle* h, double* G, int32_t ld, int32_t* kr_out);
 
+/* The work-chunk size (rows per work item of the inner-solver kernels) a
+ * handle uses, and with opts.autotune the candidates timed at create with
+ * their milliseconds per device iteration (at most cap of them; *count gets
+ * their number). */
+int sylv_adi_tuning(const sylv_handle* h, int32_t* rows_per_chunk, int32_t* cand, double* ms, int32_t cap,
+                    int32_t* count);
+
 /* Kernel statistics of a handle.  SYLV_NUM_KERNELS entries, in this order:
  * shifted product + first Gram-Schmidt sweep, second sweep, third sweep with
  * the Givens update, restart update, restart residual, controller,
@@ -432,6 +446,9 @@ int sylv_adi_batch_set_rhs(sylv_batch* b, int32_t i, const double* f, const doub
  * set-up kernel); profiling runs the host-driven loop. */
 int sylv_adi_batch_profile(sylv_batch* b, int32_t enable);
 int sylv_adi_batch_kernel_stats(const sylv_batch* b, double* ms, double* bytes, double* flops, int64_t* launches);
+/* As sylv_adi_tuning for a batch. */
+int sylv_adi_batch_tuning(const sylv_batch* b, int32_t* rows_per_chunk, int32_t* cand, double* ms, int32_t cap,
+                          int32_t* count);
 int sylv_adi_batch_destroy(sylv_batch* b);
 
 #ifdef __cplusplus

@@ -28,6 +28,7 @@ __all__ = [
     "SylvProblem", "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info",
     "sylv_adi_batch_history", "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy",
     "SylvesterADIBatch", "sylv_adi_batch_set_rhs", "sylv_adi_batch_profile", "sylv_adi_batch_kernel_stats",
+    "sylv_adi_tuning", "sylv_adi_batch_tuning",
 ]
 
 SYLV_OK = 0
@@ -49,7 +50,7 @@ EXPORTED = (
     "sylv_adi_kernel_stats", "sylv_cgs2_noalloc", "sylv_cgs2_noalloc_max_rows",
     "sylv_adi_batch_create", "sylv_adi_batch_solve", "sylv_adi_batch_info", "sylv_adi_batch_history",
     "sylv_adi_batch_factors", "sylv_adi_batch_stats", "sylv_adi_batch_destroy", "sylv_adi_batch_set_rhs",
-    "sylv_adi_batch_profile", "sylv_adi_batch_kernel_stats",
+    "sylv_adi_batch_profile", "sylv_adi_batch_kernel_stats", "sylv_adi_tuning", "sylv_adi_batch_tuning",
 )
 KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3", "restart_update", "restart_residual",
            "adi_controller", "adi_step_init", "adi_gram")
@@ -78,7 +79,7 @@ class SylvOpts(C.Structure):
                 ("max_inner", C.c_int32), ("precision", C.c_int32), ("jacobi", C.c_int32),
                 ("bl_clamp", C.c_int32), ("rows_per_chunk", C.c_int32), ("driver", C.c_int32),
                 ("ortho", C.c_int32), ("restart_every", C.c_int32), ("inner", C.c_int32),
-                ("real_pairs", C.c_int32)]
+                ("real_pairs", C.c_int32), ("autotune", C.c_int32)]
 
 
 class SylvProblem(C.Structure):
@@ -156,6 +157,8 @@ def load():
         "sylv_adi_batch_stats": ([vp, C.POINTER(C.c_int64), pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "sylv_adi_batch_destroy": ([vp], C.c_int),
         "sylv_adi_batch_set_rhs": ([vp, i32, pd, pd], C.c_int),
+        "sylv_adi_tuning": ([vp, pi32, pi32, pd, i32, pi32], C.c_int),
+        "sylv_adi_batch_tuning": ([vp, pi32, pi32, pd, i32, pi32], C.c_int),
         "sylv_adi_batch_profile": ([vp, i32], C.c_int),
         "sylv_adi_batch_kernel_stats": ([vp, pd, pd, pd, C.POINTER(C.c_int64)], C.c_int),
     }
@@ -502,6 +505,9 @@ class SylvesterADI:
     def kernel_stats(self) -> dict:
         return sylv_adi_kernel_stats(self.h)
 
+    def tuning(self) -> dict:
+        return sylv_adi_tuning(self.h)
+
     def close(self) -> None:
         if self.h:
             sylv_adi_destroy(self.h)
@@ -587,6 +593,26 @@ def sylv_adi_batch_destroy(b) -> None:
     _check(load().sylv_adi_batch_destroy(b))
 
 
+def _tuning(fn, h) -> dict:
+    chosen, count = C.c_int32(), C.c_int32()
+    cand = np.zeros(16, dtype=np.int32)
+    ms = np.zeros(16)
+    _check(fn(h, C.byref(chosen), cand.ctypes.data_as(C.POINTER(C.c_int32)),
+              ms.ctypes.data_as(C.POINTER(C.c_double)), 16, C.byref(count)))
+    k = min(count.value, 16)
+    return {"rows_per_chunk": chosen.value,
+            "candidates": {int(c): float(m) for c, m in zip(cand[:k], ms[:k])}}
+
+
+def sylv_adi_tuning(h) -> dict:
+    """Chunk size in use and the autotuner's candidates (ms per device iteration)."""
+    return _tuning(load().sylv_adi_tuning, h)
+
+
+def sylv_adi_batch_tuning(b) -> dict:
+    return _tuning(load().sylv_adi_batch_tuning, b)
+
+
 def sylv_adi_batch_set_rhs(b, i: int, f, g) -> None:
     f = np.asfortranarray(f, dtype=np.float64)
     g = np.asfortranarray(g, dtype=np.float64)
@@ -651,6 +677,9 @@ class SylvesterADIBatch:
 
     def kernel_stats(self) -> dict:
         return sylv_adi_batch_kernel_stats(self.h)
+
+    def tuning(self) -> dict:
+        return sylv_adi_batch_tuning(self.h)
 
     def close(self) -> None:
         if self.h:

@@ -117,6 +117,7 @@ int sylv_opts_default(sylv_opts* o) {
     o->restart_every = 4;
     o->inner = SYLV_INNER_GMRES;
     o->real_pairs = 0;
+    o->autotune = 0;
     return SYLV_OK;
 }
 
@@ -319,6 +320,20 @@ int sylv_adi_core(const sylv_handle* h, double* G, int32_t ld, int32_t* kr_out) 
     const int rc = h->impl->core(G, ld, &kr);
     if (kr_out) *kr_out = kr;
     return rc;
+}
+
+int sylv_adi_tuning(const sylv_handle* h, int32_t* rows_per_chunk, int32_t* cand, double* ms, int32_t cap,
+                    int32_t* count) {
+    if (!h) { set_error("null handle"); return SYLV_ERR_INVALID; }
+    if (cap > 0 && (!cand || !ms)) { set_error("null candidate buffers"); return SYLV_ERR_INVALID; }
+    return h->impl->tuning(rows_per_chunk, cand, ms, cap, count);
+}
+
+int sylv_adi_batch_tuning(const sylv_batch* b, int32_t* rows_per_chunk, int32_t* cand, double* ms, int32_t cap,
+                          int32_t* count) {
+    if (!b) { set_error("null batch"); return SYLV_ERR_INVALID; }
+    if (cap > 0 && (!cand || !ms)) { set_error("null candidate buffers"); return SYLV_ERR_INVALID; }
+    return b->impl->tuning(rows_per_chunk, cand, ms, cap, count);
 }
 
 int sylv_adi_profile(sylv_handle* h, int32_t enable) {

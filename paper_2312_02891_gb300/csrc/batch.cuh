@@ -108,6 +108,7 @@ struct Batch : BatchBase {
     std::vector<int> inst_status;
     long long launches_last = 0;
 
+    TuneResult tune;                // chunk-size autotuner (opts.autotune)
     int driver = 0;                 // 0: one CUDA graph per solve; 1: host-driven device iterations
     int restart_every = 1;
     int* h_open = nullptr;          // mapped host word (host-driven solves)
@@ -222,6 +223,17 @@ struct Batch : BatchBase {
         return rc != SYLV_OK ? rc : frc;
     }
 
+    int tuning(int* chosen, int* cand, double* ms, int cap, int* count) const override {
+        if (chosen) *chosen = rpc;
+        const int nc = (int)tune.cand.size();
+        for (int q = 0; q < nc && q < cap; ++q) {
+            if (cand) cand[q] = tune.cand[q];
+            if (ms) ms[q] = tune.ms[q];
+        }
+        if (count) *count = nc;
+        return SYLV_OK;
+    }
+
     int set_rhs(int i, const double* hf, const double* hg) override {
         if (!hf || !hg) { set_error("batch set_rhs: null f or g"); return SYLV_ERR_INVALID; }
         SYLV_CK(cudaMemcpyAsync((void*)hd[i].f, hf, (size_t)inst_n[i] * inst_r[i] * sizeof(double),
@@ -246,6 +258,30 @@ struct Batch : BatchBase {
         rpc = o.rows_per_chunk > 0 ? o.rows_per_chunk
               : o.inner == SYLV_INNER_BICGSTAB ? bicg_rows_per_chunk<T, S, C>(grows)
                                                : sweep_rows_per_chunk<T, S, C>(rows, o.ortho);
+        if (o.autotune && o.rows_per_chunk <= 0) {
+            // the systems of the batch with their operators; the Jacobi inverse
+            // is left out of the probe and the stencil pointers only identify
+            // the operators (the probe fills its own stencil values)
+            std::vector<int> tn, to;
+            std::vector<T*> tp;
+            std::vector<C*> ta;
+            std::vector<OpDesc> tops;
+            for (int i = 0; i < (int)ps.size(); ++i) {
+                const BatchProb& p = ps[i];
+                tops.push_back(p.A->desc);
+                tops.push_back(p.Bt->desc);
+                for (int side = 0; side < 2; ++side)
+                    for (int l = 0; l < p.r; ++l) {
+                        tn.push_back(side ? p.m : p.n);
+                        to.push_back(2 * i + side);
+                        tp.push_back(nullptr);
+                        const bool sc = scaled_op_possible(side ? p.Bt->desc : p.A->desc);
+                        ta.push_back(sc ? reinterpret_cast<C*>((uintptr_t)(2 * i + side + 1) * 256) : nullptr);
+                    }
+            }
+            SYLV_TRY((autotune_rpc<T, S, C>(tn, to, tops, tp, ta, o.restart, o.ortho, o.inner, s, &tune)));
+            if (tune.chosen > 0) rpc = tune.chosen;
+        }
         rpc = (rpc + 31) / 32 * 32;
         // ---- layout of every instance's buffers in one arena ----
         struct Off { size_t f, g, w, t, Z, Y, gam, hist, alpha, beta, pinvA, pinvB, avalA, avalB, gpart; };

@@ -29,6 +29,13 @@ namespace sylv {
 
 constexpr int BG_MAXCOL = 4;                     // columns of a group (the rank cap)
 constexpr int BG_PSTRIDE = 3 * BG_MAXCOL;        // partial sums per chunk (at most 3 per column)
+// Resident blocks per SM the step kernels are compiled for: they stream a
+// few vectors per row and need many loads in flight, so occupancy comes
+// before registers (the counts keep the stencil path of the product free of
+// spills for each type).
+template <typename C> struct BicgOcc { static constexpr int value = 3; };
+template <> struct BicgOcc<float> { static constexpr int value = 4; };
+template <> struct BicgOcc<cplx> { static constexpr int value = 2; };
 
 // Vectors of one BiCGstab system, column-major, ldv apart, C precision.
 enum BVec : int { BV_R = 0, BV_Q = 1, BV_P = 2, BV_V = 3, BV_T = 4, BV_RH = 5, BV_COUNT = 6 };
@@ -123,7 +130,7 @@ __device__ __forceinline__ void bicg_end_cycle(SysState<T>* st) {
 // non-finite denominator ends the cycle (breakdown) without an update.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
 k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
          const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
@@ -142,36 +149,30 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     count_work(ctl, K_SPMV, it.chunk, (double)op.nnz * sizeof(C) + 5.0 * na * sd.n * sizeof(C),
                FmaFlops<C>::v * na * ((double)op.nnz + 2.0 * sd.n));
     C beta[BG_MAXCOL];
-    const C* R[BG_MAXCOL];
-    const C* Q[BG_MAXCOL];
-    const C* RH[BG_MAXCOL];
-    C* Pv[BG_MAXCOL];
-    C* Vv[BG_MAXCOL];
 #pragma unroll
-    for (int q = 0; q < BG_MAXCOL; ++q) {
-        C* base = sd.bv + (size_t)q * BV_COUNT * ld;
+    for (int q = 0; q < BG_MAXCOL; ++q)
         beta[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].bbeta) : zero<C>();
-        R[q] = base + BV_R * ld;
-        Q[q] = base + BV_Q * ld;
-        RH[q] = base + BV_RH * ld;
-        Pv[q] = base + BV_P * ld;
-        Vv[q] = base + BV_V * ld;
-    }
+    // vector v of column q: bv + (q BV_COUNT + v) ld
+    C* __restrict__ bv = sd.bv;
+    const size_t cs = (size_t)BV_COUNT * ld;
     const T sigma = sts[g.sys0].sigma;
     C acc[BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = zero<C>();
-    auto P = [&](int q, int k) { return R[q][k] + beta[q] * Q[q][k]; };
-#pragma unroll 2
+    auto P = [&](int q, int k) {
+        const C* c = bv + q * cs + (size_t)k;
+        return c[BV_R * ld] + beta[q] * c[BV_Q * ld];
+    };
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C y[BG_MAXCOL];
         group_op_row(sd, op, sigma, i, mask, P, y);
 #pragma unroll
         for (int q = 0; q < BG_MAXCOL; ++q) {
             if (mask >> q & 1) {
-                Pv[q][i] = P(q, i);
-                Vv[q][i] = y[q];
-                acc[q] += cmul(RH[q][i], y[q]);
+                C* c = bv + q * cs + (size_t)i;
+                c[BV_P * ld] = P(q, i);
+                c[BV_V * ld] = y[q];
+                acc[q] += cmul(c[BV_RH * ld], y[q]);
             }
         }
     }
@@ -201,7 +202,7 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // when ||s|| already meets the tolerance.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
 k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
          const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
@@ -219,23 +220,19 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     count_work(ctl, K_CGS2, it.chunk, (double)op.nnz * sizeof(C) + 3.0 * na * sd.n * sizeof(C),
                FmaFlops<C>::v * na * ((double)op.nnz + 4.0 * sd.n));
     C alpha[BG_MAXCOL];
-    const C* R[BG_MAXCOL];
-    const C* Vv[BG_MAXCOL];
-    C* Tv[BG_MAXCOL];
 #pragma unroll
-    for (int q = 0; q < BG_MAXCOL; ++q) {
-        C* base = sd.bv + (size_t)q * BV_COUNT * ld;
+    for (int q = 0; q < BG_MAXCOL; ++q)
         alpha[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].balpha) : zero<C>();
-        R[q] = base + BV_R * ld;
-        Vv[q] = base + BV_V * ld;
-        Tv[q] = base + BV_T * ld;
-    }
+    C* __restrict__ bv = sd.bv;
+    const size_t cs = (size_t)BV_COUNT * ld;
     const T sigma = sts[g.sys0].sigma;
     C acc[3 * BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = zero<C>();
-    auto Sf = [&](int q, int k) { return R[q][k] - alpha[q] * Vv[q][k]; };
-#pragma unroll 2
+    auto Sf = [&](int q, int k) {
+        const C* c = bv + q * cs + (size_t)k;
+        return c[BV_R * ld] - alpha[q] * c[BV_V * ld];
+    };
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C y[BG_MAXCOL];
         group_op_row(sd, op, sigma, i, mask, Sf, y);
@@ -243,7 +240,7 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         for (int q = 0; q < BG_MAXCOL; ++q) {
             if (mask >> q & 1) {
                 const C si = Sf(q, i);
-                Tv[q][i] = y[q];
+                bv[q * cs + (size_t)BV_T * ld + i] = y[q];
                 acc[3 * q] += cmul(y[q], si);
                 acc[3 * q + 1] += from_real<C>(abs2(y[q]));
                 acc[3 * q + 2] += from_real<C>(abs2(si));
@@ -286,7 +283,7 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // beta' = (rho' / rho)(alpha / omega).
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
 k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
          const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
@@ -304,44 +301,33 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
                    7.0 * na * sd.n * sizeof(C) + 2.0 * na * sd.n * sizeof(T) + (sd.pinv ? (double)sd.n * sizeof(T) : 0.0),
                    FmaFlops<C>::v * na * 6.0 * sd.n);
         C alpha[BG_MAXCOL], omega[BG_MAXCOL];
-        C* R[BG_MAXCOL];
-        C* Q[BG_MAXCOL];
-        const C* Pv[BG_MAXCOL];
-        const C* Vv[BG_MAXCOL];
-        const C* Tv[BG_MAXCOL];
-        const C* RH[BG_MAXCOL];
         T* X[BG_MAXCOL];
 #pragma unroll
         for (int q = 0; q < BG_MAXCOL; ++q) {
-            C* base = sd.bv + (size_t)q * BV_COUNT * ld;
             const bool on = mask >> q & 1;
             alpha[q] = on ? cvt<C>(sts[g.sys0 + q].balpha) : zero<C>();
             omega[q] = on ? cvt<C>(sts[g.sys0 + q].bomega) : zero<C>();
             X[q] = on ? sts[g.sys0 + q].x : nullptr;
-            R[q] = base + BV_R * ld;
-            Q[q] = base + BV_Q * ld;
-            Pv[q] = base + BV_P * ld;
-            Vv[q] = base + BV_V * ld;
-            Tv[q] = base + BV_T * ld;
-            RH[q] = base + BV_RH * ld;
         }
+        C* __restrict__ bv = sd.bv;
+        const size_t cs = (size_t)BV_COUNT * ld;
         const T* __restrict__ pinv = sd.pinv;
         C acc[2 * BG_MAXCOL];
 #pragma unroll
         for (int q = 0; q < 2 * BG_MAXCOL; ++q) acc[q] = zero<C>();
-#pragma unroll 2
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             const T pi = pinv ? pinv[i] : make_scalar<T>(1.0, 0.0);
 #pragma unroll
             for (int q = 0; q < BG_MAXCOL; ++q) {
                 if (mask >> q & 1) {
-                    const C p = Pv[q][i], v = Vv[q][i], r = R[q][i], t = Tv[q][i];
+                    C* c = bv + q * cs + (size_t)i;
+                    const C p = c[BV_P * ld], v = c[BV_V * ld], r = c[BV_R * ld], t = c[BV_T * ld];
                     const C s = r - alpha[q] * v;
                     X[q][i] += pi * cvt<T>(alpha[q] * p + omega[q] * s);
                     const C rn = s - omega[q] * t;
-                    R[q][i] = rn;
-                    Q[q][i] = p - omega[q] * v;
-                    acc[2 * q] += cmul(RH[q][i], rn);
+                    c[BV_R * ld] = rn;
+                    c[BV_Q * ld] = p - omega[q] * v;
+                    acc[2 * q] += cmul(c[BV_RH * ld], rn);
                     acc[2 * q + 1] += from_real<C>(abs2(rn));
                 }
             }

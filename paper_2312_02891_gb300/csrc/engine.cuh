@@ -481,6 +481,138 @@ struct Engine {
 };
 
 // ---------------------------------------------------------------------------
+// Autotuner of the work-chunk size (rows per work item) of the inner-solver
+// kernels.  Each candidate builds the engine of the actual systems, fills the
+// vectors with a fixed pseudo-random pattern and the operators' stencil
+// values with a diagonally dominant stencil of the same diagonals (so the
+// iteration neither breaks down nor converges during the probe), and times
+// device iterations with CUDA events: BiCGstab 2 + 6 steps, GMRES one cycle.
+// The fastest candidate wins; every candidate and its time are kept.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_pattern(double& x, double u, double) { x = u; }
+__device__ __forceinline__ void set_pattern(float& x, double u, double) { x = (float)u; }
+__device__ __forceinline__ void set_pattern(bf16& x, double u, double) { x = __double2bfloat16(u); }
+__device__ __forceinline__ void set_pattern(cplx& x, double u, double v) { x = {u, v}; }
+__device__ __forceinline__ void set_pattern(cflt& x, double u, double v) { x = {(float)u, (float)v}; }
+__device__ __forceinline__ void set_pattern(cbf16& x, double u, double v) { x = {__double2bfloat16(u), __double2bfloat16(v)}; }
+
+template <typename X>
+__global__ void k_fill_pattern(X* v, size_t n, unsigned seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)(i * 2654435761u) ^ seed;
+        h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+        const double u = (double)(h & 0xffffff) / 16777216.0 - 0.5;
+        set_pattern(v[i], u, 0.25 - u);
+    }
+}
+
+template <typename C>
+__global__ void k_fill_stencil(C* aval, OpDesc op) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < op.n; i += gridDim.x * blockDim.x)
+        for (int d = 0; d < op.ndiag; ++d)
+            aval[(size_t)d * op.n + i] = make_scalar<C>(op.offs[d] == 0 ? 1.0 : -0.1, 0.0);
+}
+
+struct TuneResult {
+    int chosen = 0;
+    std::vector<int> cand;
+    std::vector<double> ms;      // per device iteration
+};
+
+template <typename T, typename S, typename C>
+int autotune_rpc(const std::vector<int>& sys_n, const std::vector<int>& sys_op, const std::vector<OpDesc>& ops,
+                 const std::vector<T*>& pinv, const std::vector<C*>& aval, int restart, int ortho, int inner,
+                 cudaStream_t s, TuneResult* out) {
+    // candidates: the one-wave rule and fixed sizes up to the largest system
+    std::vector<long long> rows(sys_n.begin(), sys_n.end());
+    int auto_rpc;
+    if (inner == 1) {
+        std::vector<long long> grows;
+        for (const auto& g : bicg_groups(sys_n, sys_op, pinv, aval)) grows.push_back(sys_n[g.first]);
+        auto_rpc = bicg_rows_per_chunk<T, S, C>(grows);
+    } else {
+        auto_rpc = sweep_rows_per_chunk<T, S, C>(rows, ortho);
+    }
+    const int nmax = *std::max_element(sys_n.begin(), sys_n.end());
+    std::vector<int> cand{(auto_rpc + 31) / 32 * 32};
+    for (int c : {512, 1024, 2048, 4096, 8192})
+        if (c <= std::max(nmax, 256) && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+    // synthetic stencil values for every operator that has pre-scaled diagonals
+    std::vector<Dev<C>> tav(aval.size());
+    std::vector<C*> av(aval.size(), nullptr);
+    for (size_t q = 0; q < aval.size(); ++q) {
+        if (!aval[q]) continue;
+        size_t f = q;
+        for (size_t p = 0; p < q; ++p)
+            if (aval[p] == aval[q]) { f = p; break; }
+        if (f != q) { av[q] = av[f]; continue; }
+        const OpDesc& od = ops[sys_op[q]];
+        SYLV_TRY(tav[q].alloc((size_t)od.ndiag * od.n));
+        k_fill_stencil<C><<<num_sms() * 2, 256, 0, s>>>(tav[q].p, od);
+        av[q] = tav[q].p;
+    }
+    Dev<T> xs;
+    SYLV_TRY(xs.alloc((size_t)nmax));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SYLV_CK(cudaEventCreate(&e0));
+    SYLV_CK(cudaEventCreate(&e1));
+    out->cand.clear();
+    out->ms.clear();
+    double best = 1e300;
+    int rc = SYLV_OK;
+    for (int c : cand) {
+        Engine<T, S, C> eng;
+        eng.ortho = ortho;
+        eng.inner = inner;
+        eng.pdl = 1;
+        rc = eng.setup(sys_n, sys_op, ops, pinv, av, {}, 0, restart, c, s);
+        if (rc != SYLV_OK) break;
+        const int nsys = eng.nsys;
+        if (inner == 1) {
+            k_fill_pattern<C><<<num_sms() * 4, 256, 0, s>>>(eng.d_bv.p, eng.d_bv.count, 12345u);
+        } else {
+            k_fill_pattern<S><<<num_sms() * 4, 256, 0, s>>>(eng.d_V.p, eng.d_V.count, 12345u);
+        }
+        std::vector<SysState<T>> st(nsys);
+        for (int q = 0; q < nsys; ++q) {
+            std::memset(&st[q], 0, sizeof(SysState<T>));
+            st[q].phase = PH_ARNOLDI;
+            st[q].max_iters = 1 << 30;
+            st[q].tol = 0.0;
+            st[q].x = xs.p;
+            st[q].scale[0] = 1.0;
+            st[q].g[0] = make_scalar<T>(1.0, 0.0);
+            st[q].brho = make_scalar<T>(1.0, 0.0);
+            st[q].balpha = make_scalar<T>(1.0, 0.0);
+            st[q].bomega = make_scalar<T>(1.0, 0.0);
+            st[q].bbeta = make_scalar<T>(0.5, 0.0);
+            st[q].bnorm0 = NAN;                 // no drift restart during the probe
+        }
+        SYLV_CK(cudaMemcpyAsync(eng.d_st.p, st.data(), nsys * sizeof(SysState<T>), cudaMemcpyHostToDevice, s));
+        BatchCtl cc{};
+        cc.n_active = nsys;
+        cc.nitems = eng.nitems;
+        SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &cc, sizeof(cc), cudaMemcpyHostToDevice, s));
+        const int warm = inner == 1 ? 2 : 0, timed = inner == 1 ? 6 : std::max(1, restart - 1);
+        for (int t = 0; t < warm; ++t) SYLV_TRY(eng.launch_tick(0, 0, false));
+        SYLV_CK(cudaEventRecord(e0, s));
+        for (int t = 0; t < timed; ++t) SYLV_TRY(eng.launch_tick(0, 0, false));
+        SYLV_CK(cudaEventRecord(e1, s));
+        SYLV_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SYLV_CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / timed;
+        out->cand.push_back(c);
+        out->ms.push_back(per);
+        if (per < best) { best = per; out->chosen = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SYLV_CK(cudaStreamSynchronize(s));
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // Standalone entry points for one operator: batched GMRES, CGS2, product.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -767,6 +899,7 @@ struct Adi : AdiBase {
     Dev<T> w, t, Z, Y, gam, alpha, beta, pinvA, pinvB, gpart;
     Dev<C> avalA, avalB;
     Dev<AdiState<T>> st;
+    TuneResult tune;                // chunk-size autotuner (opts.autotune)
     // real double steps of conjugate pairs (complex shifts, opts.real_pairs)
     int real_pairs = 0;
     Dev<T> XA, XB, XA2, XB2;
@@ -808,9 +941,9 @@ struct Adi : AdiBase {
         for (int l = 0; l < r; ++l) { rows.push_back(n); rows.push_back(m); }
         // BiCGstab: the r columns of each side form one group
         const std::vector<long long> grows{(long long)n, (long long)m};
-        const int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
-                        : a.o.inner == SYLV_INNER_BICGSTAB ? bicg_rows_per_chunk<T, S, C>(grows)
-                                                           : sweep_rows_per_chunk<T, S, C>(rows, a.o.ortho);
+        int rpc = a.o.rows_per_chunk > 0 ? a.o.rows_per_chunk
+                  : a.o.inner == SYLV_INNER_BICGSTAB ? bicg_rows_per_chunk<T, S, C>(grows)
+                                                     : sweep_rows_per_chunk<T, S, C>(rows, a.o.ortho);
         real_pairs = (a.o.real_pairs && sizeof(T) == sizeof(cplx)) ? 1 : 0;
         // a pair that starts at step kmax ends at kmax + 1
         const int ksl = kmax + real_pairs;
@@ -866,6 +999,10 @@ struct Adi : AdiBase {
         std::vector<OpDesc> ops{a.A->desc, a.Bt->desc};
         eng.ortho = a.o.ortho;
         eng.inner = a.o.inner;
+        if (a.o.autotune && a.o.rows_per_chunk <= 0) {
+            SYLV_TRY((autotune_rpc<T, S, C>(sn, so, ops, pv, av, a.o.restart, a.o.ortho, a.o.inner, stream, &tune)));
+            if (tune.chosen > 0) rpc = tune.chosen;
+        }
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, a.o.restart, rpc, stream));
         const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
         SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
@@ -1119,6 +1256,17 @@ struct Adi : AdiBase {
     }
 
     int is_real() const override { return sizeof(T) == sizeof(double) || real_pairs; }
+
+    int tuning(int* chosen, int* cand, double* ms, int cap, int* count) const override {
+        if (chosen) *chosen = tune.chosen > 0 ? tune.chosen : eng.h_sd[0].rows_per_chunk;
+        const int nc = (int)tune.cand.size();
+        for (int q = 0; q < nc && q < cap; ++q) {
+            if (cand) cand[q] = tune.cand[q];
+            if (ms) ms[q] = tune.ms[q];
+        }
+        if (count) *count = nc;
+        return SYLV_OK;
+    }
 
     int core(double* G, int ld, int* kr) const override {
         AdiState<T> s;

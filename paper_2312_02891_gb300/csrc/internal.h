@@ -72,6 +72,7 @@ struct AdiBase {
     virtual int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const = 0;
     virtual int core(double* G, int ld, int* kr) const = 0;
     virtual int is_real() const = 0;     // factors are real (real shifts or real double steps)
+    virtual int tuning(int* chosen, int* cand, double* ms, int cap, int* count) const = 0;
 };
 
 struct AdiArgs {
@@ -114,6 +115,7 @@ struct BatchBase {
     virtual int profile(int on) = 0;
     virtual int kernel_stats(double* ms, double* bytes, double* flops, long long* launches) const = 0;
     virtual int set_rhs(int i, const double* f, const double* g) = 0;
+    virtual int tuning(int* chosen, int* cand, double* ms, int cap, int* count) const = 0;
 };
 
 // One instantiation per (shift type, precision): r = real shifts, c = complex

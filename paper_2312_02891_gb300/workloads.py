@@ -275,12 +275,17 @@ def select_shift_pairs(cand_a: np.ndarray, cand_b: np.ndarray, count: int,
             out = out * np.abs((mu - b) / (mu + a))
         return out
 
+    # first pair: for each alpha, all betas at once (the same elementwise
+    # operations as phiA / phiB for one pair, so the values and the first
+    # minimum in (alpha, beta) order are those of the plain double loop)
     best = None
     for a in ca:
-        for b in cb:
-            val = phiA(ca, [a], [b]).max() * phiB(cb, [a], [b]).max()
-            if best is None or val < best[0]:
-                best = (val, a, b)
+        ma = np.abs((ca[None, :] - a) / (ca[None, :] + cb[:, None])).max(axis=1)
+        mb = np.abs((cb[None, :] - cb[:, None]) / (cb[None, :] + a)).max(axis=1)
+        val = ma * mb
+        j = int(np.argmin(val))
+        if best is None or val[j] < best[0]:
+            best = (val[j], a, cb[j])
     al, be = [best[1]], [best[2]]
 
     def add(a, b):
@@ -477,22 +482,43 @@ def problem_config(which: str) -> Problem:
     raise ValueError(f"unknown workload {which!r}")
 
 
-def batch_problems(count: int, base_seed: int = 1000, n_shifts: int = 10, nmin: int = 64, nmax: int = 256):
+def _batch_instance(i: int, base_seed: int, n_shifts: int, nmin: int, nmax: int) -> Problem:
+    span = nmax - nmin + 1
+    s = base_seed + i
+    u = _uniform53(s, 9, 0, 0, 5)
+    NA = nmin + int(u[0] * span)
+    NB = nmin + int(u[1] * span)
+    r = (1, 2, 4)[int(u[2] * 3)]
+    magA, magB = 50.0 * u[3], 50.0 * u[4]
+    return make_problem(f"batch{i}", NA, 2, "xy", magA, NB, 2, "rot2", magB, r, s,
+                        n_shifts, sampled_shifts=True, restart=30, jacobi=True)
+
+
+def batch_problems(count: int, base_seed: int = 1000, n_shifts: int = 10, nmin: int = 64, nmax: int = 256,
+                   workers: int = 1):
     """Independent 2D instances with N_A, N_B ~ U{nmin..nmax} (64..256 for the
     batched workload), r in {1,2,4}, convection magnitudes ~ U[0,50]
     (directions (x,y) for A, (y,-x) for B); instance i uses seed base_seed + i.
     Shifts: select_real_shifts_sampled (with the plain greedy selection six
     of the 64 instances do not reach tau in 50 steps even with exact inner
-    solves)."""
-    out = []
-    span = nmax - nmin + 1
-    for i in range(count):
-        s = base_seed + i
-        u = _uniform53(s, 9, 0, 0, 5)
-        NA = nmin + int(u[0] * span)
-        NB = nmin + int(u[1] * span)
-        r = (1, 2, 4)[int(u[2] * 3)]
-        magA, magB = 50.0 * u[3], 50.0 * u[4]
-        out.append(make_problem(f"batch{i}", NA, 2, "xy", magA, NB, 2, "rot2", magB, r, s,
-                                n_shifts, sampled_shifts=True, restart=30, jacobi=True))
-    return out
+    solves).  workers > 1 generates the instances in that many spawned
+    processes (the same instances: each depends only on its seed)."""
+    args = [(i, base_seed, n_shifts, nmin, nmax) for i in range(count)]
+    if workers <= 1 or count <= 1:
+        return [_batch_instance(*a) for a in args]
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    # one BLAS thread per process (the processes already fill the cores)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with ProcessPoolExecutor(max_workers=min(workers, count), mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_instance, *zip(*args)))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

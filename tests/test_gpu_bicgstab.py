@@ -192,12 +192,18 @@ def test_lradi_with_bicgstab_matches_oracle(name, strategy, jacobi, precision):
         ito = ref.inner_its_A + ref.inner_its_B
         assert abs(itg - ito) <= 0.02 * ito + 4 * info["steps"], (itg, ito)
         # BiCGstab's residual is not monotone: the step that meets the
-        # tolerance, and with it the achieved residual, can differ by one step
-        # between two roundings of the same recurrences (the back-looking rule
-        # feeds the achieved residuals into the next tolerances)
+        # tolerance, and with it the achieved residual, can differ between two
+        # roundings of the same recurrences.  Every step meets its requested
+        # tolerances; without back-looking the tolerances depend only on
+        # ||w||, ||t|| and follow the oracle's (back-looking feeds the achieved
+        # residuals into the next tolerances, so there they drift apart)
         ks = min(len(hist), len(ref.history))
         for i in range(ks):
-            assert hist[i][12] == pytest.approx(ref.history[i]["res_comp"], rel=2e-2, abs=1e-3 * p.tau)
+            h, o = hist[i], ref.history[i]
+            assert h[6] <= h[3] * (1 + 1e-9) and h[7] <= h[4] * (1 + 1e-9)
+            if not strategy.startswith("bl_"):
+                assert h[3] == pytest.approx(o["dA"], rel=1e-3) and h[4] == pytest.approx(o["dB"], rel=1e-3)
+                assert h[12] == pytest.approx(o["res_comp"], rel=2e-2, abs=1e-3 * p.tau)
 
 
 def test_graph_and_host_drivers_agree_with_bicgstab():

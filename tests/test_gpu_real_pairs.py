@@ -85,11 +85,15 @@ def test_real_double_step_matches_oracle(name, inner, precision, strategy):
         if h["pair"]:
             assert np.allclose(blk, np.kron(blk[::r, ::r], np.eye(r)), rtol=1e-12, atol=0)
         c0 += s
-    if precision == "fp64":
-        # per step of the equivalent complex formulation: the residual norms of
-        # both steps of a pair (the inputs of eq. (upd_resgap))
-        rows = [(h["nrA"][j], h["nrB"][j]) for h in ref.history for j in range(2 if h["pair"] else 1)]
-        ks = min(len(rows), len(hist))
+    # per step of the equivalent complex formulation: the residual norms of
+    # both steps of a pair (the inputs of eq. (upd_resgap)) meet the step's
+    # tolerances; with GMRES in float64 they are the oracle's (BiCGstab's
+    # achieved residuals differ with the rounding, see test_gpu_bicgstab.py)
+    rows = [(h["nrA"][j], h["nrB"][j]) for h in ref.history for j in range(2 if h["pair"] else 1)]
+    ks = min(len(rows), len(hist))
+    for i in range(ks):
+        assert hist[i][6] <= hist[i][3] * (1 + 1e-9) and hist[i][7] <= hist[i][4] * (1 + 1e-9)
+    if precision == "fp64" and inner == "gmres":
         for i in range(min(ks, 6)):
             assert hist[i][6] == pytest.approx(rows[i][0], rel=1e-3, abs=1e-3 * p.tau)
             assert hist[i][7] == pytest.approx(rows[i][1], rel=1e-3, abs=1e-3 * p.tau)
