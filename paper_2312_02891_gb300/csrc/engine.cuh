@@ -1006,7 +1006,8 @@ struct Adi : AdiBase {
         SYLV_TRY(eng.setup(sn, so, ops, pv, av, {}, 0, a.o.restart, rpc, stream));
         const int nchA = (n + rpc - 1) / rpc, nchB = (m + rpc - 1) / rpc;
         SYLV_TRY(gpart.alloc((size_t)(nchA + nchB) * SYLV_GSTRIDE));
-        if (real_pairs) SYLV_TRY(pgpart.alloc((size_t)(nchA + nchB) * SYLV_PGSTRIDE));
+        // chunk partials, then the two reduced Gram sets of k_adi_pair_finish
+        if (real_pairs) SYLV_TRY(pgpart.alloc((size_t)(nchA + nchB + 2) * SYLV_PGSTRIDE));
         SYLV_CK(cudaHostAlloc((void**)&h_done, sizeof(int), cudaHostAllocMapped));
         *h_done = 0;
         SYLV_CK(cudaHostGetDevicePointer((void**)&d_hdone, h_done, 0));
@@ -1214,10 +1215,22 @@ struct Adi : AdiBase {
 
     int launch_pair_update(int nb) {
         switch (r) {
-            case 1: k_adi_pair_update<T, S, C, 1><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
-            case 2: k_adi_pair_update<T, S, C, 2><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
-            case 3: k_adi_pair_update<T, S, C, 3><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
-            default: k_adi_pair_update<T, S, C, 4><<<nb, SYLV_BLOCK, 0, stream>>>(d); break;
+            case 1:
+                k_adi_pair_update<T, S, C, 1><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+                k_adi_pair_finish<T, S, C, 1><<<1, 32, 0, stream>>>(d);
+                break;
+            case 2:
+                k_adi_pair_update<T, S, C, 2><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+                k_adi_pair_finish<T, S, C, 2><<<1, 32, 0, stream>>>(d);
+                break;
+            case 3:
+                k_adi_pair_update<T, S, C, 3><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+                k_adi_pair_finish<T, S, C, 3><<<1, 32, 0, stream>>>(d);
+                break;
+            default:
+                k_adi_pair_update<T, S, C, 4><<<nb, SYLV_BLOCK, 0, stream>>>(d);
+                k_adi_pair_finish<T, S, C, 4><<<1, 32, 0, stream>>>(d);
+                break;
         }
         SYLV_CK(cudaGetLastError());
         eng.launches[K_GRAM]++;

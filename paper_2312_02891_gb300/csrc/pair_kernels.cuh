@@ -101,8 +101,11 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_pair_mid(AdiDev<T, S, C> d) 
 
 // Complex r x r Hermitian Gram of the combination c1 X1 + c2 X2 of two real
 // n x r blocks whose joint 2r x 2r Gram is G (row-major, leading dimension 2R).
+// Kept out of line: with r = 4 and all eight calls inlined into
+// k_adi_pair_finish the kernel returned wrong norms (checked against host
+// eigenvalues of the same Grams); out of line it agrees.
 template <int R>
-__device__ double combo_gram_lmax(const double* G, cplx c1, cplx c2) {
+__device__ __noinline__ double combo_gram_lmax(const double* G, cplx c1, cplx c2) {
     cplx H[SYLV_MAXR * SYLV_MAXR];
     for (int q = 0; q < SYLV_MAXR * SYLV_MAXR; ++q) H[q] = cplx{0.0, 0.0};
     for (int a = 0; a < R; ++a)
@@ -216,11 +219,27 @@ __global__ void __launch_bounds__(SYLV_BLOCK) k_adi_pair_update(AdiDev<T, S, C> 
     }
     if (e < NG) d.pgpart[(size_t)bi * SYLV_PGSTRIDE + e] = acc;
     if (!last_block(&s->counter, d.nchA + d.nchB)) return;
-    __shared__ double GA[NG], GB[NG];
-    reduce_chunks(d.pgpart, d.nchA, SYLV_PGSTRIDE, NG, GA);
-    reduce_chunks(d.pgpart + (size_t)d.nchA * SYLV_PGSTRIDE, d.nchB, SYLV_PGSTRIDE, NG, GB);
-    if (threadIdx.x != 0) return;
-    s->counter = 0;
+    // the reduced Grams go to the slots after the chunk partials; the scalar
+    // evaluation runs in k_adi_pair_finish (one small block)
+    double* GAg = d.pgpart + (size_t)(d.nchA + d.nchB) * SYLV_PGSTRIDE;
+    reduce_chunks(d.pgpart, d.nchA, SYLV_PGSTRIDE, NG, GAg);
+    reduce_chunks(d.pgpart + (size_t)d.nchA * SYLV_PGSTRIDE, d.nchB, SYLV_PGSTRIDE, NG, GAg + SYLV_PGSTRIDE);
+    if (threadIdx.x == 0) s->counter = 0;
+}
+
+// The scalar part of the pair update (thread 0): eq. (upd_resgap) for both
+// steps of a pair from the reduced Grams, the history rows, the 2 x 2 core,
+// the residual norm ||w t^*|| and the outer stop test.
+template <typename T, typename S, typename C, int R>
+__global__ void k_adi_pair_finish(AdiDev<T, S, C> d) {
+    AdiState<T>* s = d.s;
+    if (s->done || threadIdx.x != 0) return;
+    constexpr int NW = R * R, NA = 4 * R * R;
+    const double* GA = d.pgpart + (size_t)(d.nchA + d.nchB) * SYLV_PGSTRIDE;
+    const double* GB = GA + SYLV_PGSTRIDE;
+    const int k = s->k;
+    const bool pair = s->pair != 0;
+    const cplx gam = to_cplx(s->gamma_k);
     const double ag = absv(gam);
     // inner steps: the first solves of a pair were counted by k_adi_pair_mid
     long long itA = pair ? s->pitsA : 0, itB = pair ? s->pitsB : 0, cyc = 0;
