@@ -7,6 +7,8 @@ writes tests/golden/<workload>_<strategy>.json with the outer step count,
 the per-step controller history, inner iteration totals, the computed and
 true relative residuals, and a two-sided sketch S = P^T X Q of the factored
 solution (P: n x 16, Q: m x 16 seeded Gaussian, streams 5 and 6).
+``python tests/golden/make_golden.py batch64 nobl_mid bicgstab`` writes the
+same per instance of the 64-instance batched workload (8 x 8 sketches).
 """
 from __future__ import annotations
 
@@ -65,11 +67,57 @@ def main(workload: str, strategy: str, **extra):
     print(path, res.steps, res.res_comp, tr, res.inner_its_A, res.inner_its_B, f"{wall:.0f}s")
 
 
+BATCH_SKETCH = 8
+
+
+def _batch_one(i, strategy, inner):
+    """Oracle solve of instance i of the 64-instance batched workload."""
+    p = W.batch_problems(1, base_seed=1000 + i)[0]
+    t0 = time.time()
+    res = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy=strategy, jacobi=True, inner=inner)
+    wall = time.time() - t0
+    A, B = p.A.to_scipy(), p.B.to_scipy()
+    nfg = lowrank_norm2(p.f, p.g)
+    tr = true_residual_norm2(A, B, p.f, p.g, res.Z, res.gamma, res.Y) / nfg
+    P = np.stack([W.normal(12345, 5, c, p.A.n) for c in range(BATCH_SKETCH)], axis=1)
+    Q = np.stack([W.normal(12345, 6, c, p.B.n) for c in range(BATCH_SKETCH)], axis=1)
+    S = sketch(res.Z, res.gamma, res.Y, P, Q)
+    return dict(instance=i, n=p.A.n, m=p.B.n, r=p.r, steps=res.steps, converged=bool(res.converged),
+                res_comp=res.res_comp, res_true=tr, inner_its=res.inner_its_A + res.inner_its_B,
+                sketch=np.real(S).tolist(), oracle_wall_s=wall)
+
+
+def main_batch(strategy: str, inner: str, count: int = 64, workers: int = 8):
+    """tests/golden/batch64_<strategy>_<inner>.json: per instance of the
+    batched workload the outer steps, residuals and an 8 x 8 sketch of X."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    t0 = time.time()
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        rows = list(ex.map(_batch_one, range(count), [strategy] * count, [inner] * count))
+    out = dict(workload="batch64", strategy=strategy, inner=inner, tau=1e-8, sketch_cols=BATCH_SKETCH,
+               instances=rows, oracle_wall_s=time.time() - t0)
+    path = os.path.join(HERE, f"batch64_{strategy}_{inner}.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=0)
+    print(path, sum(r["steps"] for r in rows), f"{time.time() - t0:.0f}s")
+
+
 if __name__ == "__main__":
+    if len(sys.argv) > 1 and sys.argv[1] == "batch64":
+        main_batch(sys.argv[2] if len(sys.argv) > 2 else "nobl_mid", sys.argv[3] if len(sys.argv) > 3 else "bicgstab")
+        sys.exit(0)
     wl = sys.argv[1] if len(sys.argv) > 1 else "mid2d"
     st = sys.argv[2] if len(sys.argv) > 2 else "bl_mid"
     kw = {}
     for a in sys.argv[3:]:
         k, v = a.split("=")
-        kw[k] = float(v) if "." in v or "e" in v else int(v)
+        for conv in (int, float, str):
+            try:
+                kw[k] = conv(v)
+                break
+            except ValueError:
+                continue
     main(wl, st, **kw)

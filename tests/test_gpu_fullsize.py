@@ -121,3 +121,50 @@ def test_mid2d_literal_back_looking_stagnates_like_the_oracle(mid):
     st, info, hist, _ = solve(mid, strategy="bl_mid", precision="fp64", driver=1)
     assert st == -4 and info["steps"] == g["steps"] == 50
     assert info["rel_res_comp"] == pytest.approx(g["res_comp"], rel=1e-2)
+
+
+# ---------------------------------------------------------------- the batched workload at full size
+
+@pytest.fixture(scope="module")
+def batch64():
+    return W.batch_problems(64, workers=min(16, os.cpu_count() or 1))
+
+
+@pytest.mark.parametrize("opts", [dict(precision="fp32", inner="bicgstab", autotune=1),
+                                  dict(precision="fp64", inner="bicgstab")])
+def test_batch64_matches_stored_oracle_runs(batch64, opts):
+    """All 64 instances of the batched workload (n, m from 4356 to 65536,
+    r in {1, 2, 4}) against the stored oracle run of each instance
+    (tests/golden/batch64_nobl_mid_bicgstab.json): outer steps within +-1,
+    the computed residual below tau, the true residual of the GPU factors
+    (evaluated by the oracle) within the computed residual plus u + v (the
+    residual-gap bound of eq. (upd_resgap)), and the 8 x 8 sketch P^T X Q
+    close to the oracle's.  BiCGstab stops each inner solve somewhere below
+    its tolerance, so two valid runs differ by solution errors of order
+    tau times the conditioning of the Sylvester operator (2.6e-5 relative
+    seen); the sketch bound 1e-3 only says it is the same solution."""
+    g = golden("batch64_nobl_mid_bicgstab")
+    ng = g["sketch_cols"]
+    worst = 0.0
+    with P.SylvesterADIBatch(batch64, strategy="nobl_mid", jacobi=1, **opts) as bt:
+        assert bt.solve() == 0, P.sylv_last_error()
+        for p, gi in zip(batch64, g["instances"]):
+            i = gi["instance"]
+            info = bt.info(i)
+            assert (p.A.n, p.B.n, p.r) == (gi["n"], gi["m"], gi["r"])
+            assert abs(info["steps"] - gi["steps"]) <= 1, (i, info["steps"], gi["steps"])
+            assert info["rel_res_comp"] < p.tau
+            Z, Y, gam = bt.factors(i)
+            nfg = lowrank_norm2(p.f, p.g)
+            last = bt.history(i)[info["steps"] - 1]
+            tr = true_residual_norm2(p.A.to_scipy(), p.B.to_scipy(), p.f, p.g, Z, gam, Y)
+            assert tr <= info["rel_res_comp"] * nfg + (last[10] + last[11]) * (1 + 1e-6) + 1e-12 * nfg, \
+                (i, tr / nfg, info["rel_res_comp"], (last[10] + last[11]) / nfg)
+            Pm = np.stack([W.normal(12345, 5, c, p.A.n) for c in range(ng)], axis=1)
+            Qm = np.stack([W.normal(12345, 6, c, p.B.n) for c in range(ng)], axis=1)
+            S = np.real((Pm.T @ Z) @ (gam[:, None] * (Y.conj().T @ Qm)))
+            Sg = np.array(gi["sketch"])
+            rel = np.linalg.norm(S - Sg) / np.linalg.norm(Sg)
+            worst = max(worst, rel)
+            assert rel <= 1e-3, (i, rel)
+    print("batch64 %s: largest relative sketch difference %.2e" % (opts, worst))
