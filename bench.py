@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"], help="GMRES orthogonalisation")
     ap.add_argument("--real-pairs", type=int, default=1, help="real double steps for complex shift pairs")
     ap.add_argument("--kmax", type=int, default=50, help="outer step cap (small values give short profiler cases)")
+    ap.add_argument("--rows-per-chunk", type=int, default=0,
+                    help="fixed rows per work item (0: autotuned; a fixed value gives profiler runs without the probe)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--clock-log", default=os.path.join(tempfile.gettempdir(), "sylv_clocks_rank{rank}.csv"),
@@ -282,8 +284,15 @@ KNAMES = {
 INNER_KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
 # DRAM traffic / algorithmic bytes of a kernel from one ncu capture of the
 # current kernels on the same workload, keyed by (inner solver, kernel); a
-# kernel changed after its capture has no entry (traffic null)
-NCU_TRAFFIC_RATIO = {}
+# kernel changed after its capture has no entry (traffic null).  BiCGstab:
+# one launch of each step kernel with every column system of the batched
+# workload active (dram__bytes_read.sum + dram__bytes_write.sum over the
+# kernel's own byte model), profiles/bicgstab_batch64_fp32.md.
+NCU_TRAFFIC_RATIO = {
+    ("bicgstab", "arnoldi_spmv"): 259.186688 / 239.5,     # k_bicg_a
+    ("bicgstab", "cgs_pass2"): 157.722112 / 171.5,        # k_bicg_b
+    ("bicgstab", "cgs_pass3"): 364.116224 / 402.2,        # k_bicg_c
+}
 
 
 def kernel_table(stats, names):
@@ -361,13 +370,15 @@ def run_ours(a):
 
     def make_batch(**kw):
         o = dict(strategy=a.strategy, precision=a.precision, jacobi=1, restart=30, inner=a.inner,
-                 ortho="cgs2" if a.inner == "bicgstab" else a.ortho, kmax=a.kmax, autotune=1)
+                 ortho="cgs2" if a.inner == "bicgstab" else a.ortho, kmax=a.kmax,
+                 autotune=0 if a.rows_per_chunk else 1, rows_per_chunk=a.rows_per_chunk)
         o.update(kw)
         return P.SylvesterADIBatch(probs, stream=stream, **o)
 
     def make_single(p, **kw):
         o = dict(strategy=a.strategy, precision=a.precision, jacobi=int(p.opts.get("jacobi", False)),
-                 restart=p.opts.get("restart", 30), inner=a.inner, ortho=a.ortho, kmax=a.kmax, autotune=1)
+                 restart=p.opts.get("restart", 30), inner=a.inner, ortho=a.ortho, kmax=a.kmax,
+                 autotune=0 if a.rows_per_chunk else 1, rows_per_chunk=a.rows_per_chunk)
         if np.iscomplexobj(p.alpha) or np.iscomplexobj(p.beta):
             o["real_pairs"] = a.real_pairs
         o.update(kw)
