@@ -399,11 +399,15 @@ struct Batch : BatchBase {
         return SYLV_OK;
     }
 
-    // WHILE(h_loop) { outer -> step -> spmv -> pass2 -> pass3 -> IF(h_restart) { update -> residual } }
+    // WHILE(h_loop) { IF(h_bouter) { outer -> step } -> spmv -> pass2 -> pass3 ->
+    //                 IF(h_restart) { update -> residual } }
     // h_loop starts at 1 on each launch; afterwards only the grid-level
     // decisions of pass 3 / the restart residual keep it set (sweep 1 clears
     // it first), and they keep it while a system is active or an instance
-    // has not finished.
+    // has not finished.  h_bouter starts at 1 (every instance takes its
+    // initial Grams); sweep 1 clears it and a system that finishes sets it,
+    // so the outer-step kernels run only in the device iterations after one
+    // did (an instance moves on only when all its systems are done).
     int build_graph() {
         cudaGraph_t g;
         SYLV_CK(cudaGraphCreate(&g, 0));
@@ -419,6 +423,8 @@ struct Batch : BatchBase {
         SYLV_CK(cudaGraphAddNode(&n_loop, g, nullptr, nullptr, 0, &lp));
         cudaGraph_t body = lp.conditional.phGraph_out[0];
         SYLV_CK(cudaGraphConditionalHandleCreate(&h_restart, body, 0, cudaGraphCondAssignDefault));
+        cudaGraphConditionalHandle h_bouter;
+        SYLV_CK(cudaGraphConditionalHandleCreate(&h_bouter, body, 1, cudaGraphCondAssignDefault));
         auto* dsp = d_ds.p;
         auto* bip = d_items.p;
         auto* sdp = eng.d_sd.p;
@@ -436,9 +442,17 @@ struct Batch : BatchBase {
         void* a4[] = {&sdp, &stp, &itp, &ctp};
         void* a5[] = {&sdp, &stp, &opp, &itp, &ctp};
         const int ni = eng.nitems;
-        cudaGraphNode_t n_o, n_s, n1, n2, n3, n_if, n4, n5;
-        SYLV_TRY(add_kernel(&n_o, body, nullptr, (void*)k_batch_outer<T, S, C>, nbitems, ao));
-        SYLV_TRY(add_kernel(&n_s, body, &n_o, (void*)k_batch_step<T, S, C>, nbitems, ao));
+        cudaGraphNode_t n_o, n_s, n1, n2, n3, n_if, n4, n5, n_ob;
+        cudaGraphNodeParams op = {};
+        op.type = cudaGraphNodeTypeConditional;
+        op.conditional.handle = h_bouter;
+        op.conditional.type = cudaGraphCondTypeIf;
+        op.conditional.size = 1;
+        SYLV_CK(cudaGraphAddNode(&n_ob, body, nullptr, nullptr, 0, &op));
+        cudaGraph_t ob_body = op.conditional.phGraph_out[0];
+        SYLV_TRY(add_kernel(&n_o, ob_body, nullptr, (void*)k_batch_outer<T, S, C>, nbitems, ao));
+        SYLV_TRY(add_kernel(&n_s, ob_body, &n_o, (void*)k_batch_step<T, S, C>, nbitems, ao));
+        n_s = n_ob;               // the inner kernels follow the IF node
         const int sm = sweep_smem_bytes<S, C>();
         auto* grp = eng.d_groups.p;
         auto* gip = eng.d_gitems.p;
@@ -477,6 +491,8 @@ struct Batch : BatchBase {
         SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
         c.h_loop = h_loop;
         c.h_restart = h_restart;
+        c.h_bouter = h_bouter;
+        c.bouter = 1;
         c.nsys = eng.nsys;
         SYLV_CK(cudaMemcpy(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         return SYLV_OK;

@@ -69,7 +69,7 @@ __device__ __forceinline__ void group_op_row(const SysDesc<T, S, C>& sd, const O
             if (d < op.ndiag) {
                 const int k = i + op.offs[d];
                 if (k >= 0 && k < op.n) {
-                    const C a = av[(size_t)d * op.n + i];
+                    const C a = ldro(av + (size_t)d * op.n + i);
 #pragma unroll
                     for (int q = 0; q < BG_MAXCOL; ++q)
                         if (mask >> q & 1) y[q] += a * X(q, k);
@@ -135,7 +135,10 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
          const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_SPMV);
-    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ctl->h_loop, 0u);
+    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) {
+        cudaGraphSetConditional(ctl->h_loop, 0u);
+        if (ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 0u);
+    }
     const Item it = items[blockIdx.x];
     const BGroup<T> g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
@@ -159,9 +162,10 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     C acc[BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = zero<C>();
+    // r, q, rhat and the stencil are not written here: read-only loads
     auto P = [&](int q, int k) {
         const C* c = bv + q * cs + (size_t)k;
-        return c[BV_R * ld] + beta[q] * c[BV_Q * ld];
+        return ldro(c + BV_R * ld) + beta[q] * ldro(c + BV_Q * ld);
     };
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C y[BG_MAXCOL];
@@ -172,7 +176,7 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
                 C* c = bv + q * cs + (size_t)i;
                 c[BV_P * ld] = P(q, i);
                 c[BV_V * ld] = y[q];
-                acc[q] += cmul(c[BV_RH * ld], y[q]);
+                acc[q] += cmul(ldro(c + BV_RH * ld), y[q]);
             }
         }
     }
@@ -229,9 +233,10 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     C acc[3 * BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = zero<C>();
+    // r, v and the stencil are not written here: read-only loads
     auto Sf = [&](int q, int k) {
         const C* c = bv + q * cs + (size_t)k;
-        return c[BV_R * ld] - alpha[q] * c[BV_V * ld];
+        return ldro(c + BV_R * ld) - alpha[q] * ldro(c + BV_V * ld);
     };
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         C y[BG_MAXCOL];
@@ -315,19 +320,24 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         C acc[2 * BG_MAXCOL];
 #pragma unroll
         for (int q = 0; q < 2 * BG_MAXCOL; ++q) acc[q] = zero<C>();
+        // every element is read and then overwritten by the same thread only:
+        // read-only loads, so the next row's loads may pass this row's stores
+#pragma unroll 2
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const T pi = pinv ? pinv[i] : make_scalar<T>(1.0, 0.0);
+            const T pi = pinv ? ldro(pinv + i) : make_scalar<T>(1.0, 0.0);
 #pragma unroll
             for (int q = 0; q < BG_MAXCOL; ++q) {
                 if (mask >> q & 1) {
                     C* c = bv + q * cs + (size_t)i;
-                    const C p = c[BV_P * ld], v = c[BV_V * ld], r = c[BV_R * ld], t = c[BV_T * ld];
+                    const C p = ldro(c + BV_P * ld), v = ldro(c + BV_V * ld), r = ldro(c + BV_R * ld);
+                    const C t = ldro(c + BV_T * ld), rh = ldro(c + BV_RH * ld);
+                    const T xo = ldro(X[q] + i);
                     const C s = r - alpha[q] * v;
-                    X[q][i] += pi * cvt<T>(alpha[q] * p + omega[q] * s);
+                    X[q][i] = xo + pi * cvt<T>(alpha[q] * p + omega[q] * s);
                     const C rn = s - omega[q] * t;
                     c[BV_R * ld] = rn;
                     c[BV_Q * ld] = p - omega[q] * v;
-                    acc[2 * q] += cmul(c[BV_RH * ld], rn);
+                    acc[2 * q] += cmul(rh, rn);
                     acc[2 * q + 1] += from_real<C>(abs2(rn));
                 }
             }

@@ -167,6 +167,19 @@ __device__ __forceinline__ cplx ldcg(const cplx* p) {
     double2 v = __ldcg(reinterpret_cast<const double2*>(p));
     return {v.x, v.y};
 }
+// Loads through the read-only (non-coherent) path: for data that no thread of
+// the kernel writes, or that only the loading thread overwrites afterwards.
+// They let the compiler move the next row's loads ahead of this row's stores.
+__device__ __forceinline__ float ldro(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldro(const double* p) { return __ldg(p); }
+__device__ __forceinline__ cflt ldro(const cflt* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cplx ldro(const cplx* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
 
 // ---------------------------------------------------------------------------
 // Sparse operator: stored by diagonals (finite-difference stencils) or CSR.
@@ -378,6 +391,11 @@ struct BatchCtl {
     int n_inst_open;        // batched solves: instances not finished (0 for a single solve)
     int* h_open;            // batched solves, host-driven: mapped host word cleared when n_inst_open reaches 0
     int nitems;             // work items of the batch (grid-stride kernels)
+    // batched graph: IF node around the outer-step kernels, set when a column
+    // system finishes (an instance may then take its outer step), cleared by
+    // the first inner kernel of every device iteration
+    int bouter;             // 1 when h_bouter belongs to the running graph
+    cudaGraphConditionalHandle h_bouter;
 };
 
 __device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {

@@ -139,6 +139,7 @@ __device__ __forceinline__ void givens(T a, T b, double& c, T& s) {
 template <typename T>
 __device__ void mark_done(SysState<T>* st, BatchCtl* ctl) {
     st->phase = PH_DONE;
+    if (ctl->graph && ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 1u);
     int old = atomicSub(&ctl->n_active, 1);
     if (old == 1 && ctl->h_flag) {
         *(volatile int*)ctl->h_flag = 0;
@@ -386,7 +387,10 @@ k_arnoldi_spmv(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restric
     count_launch(ctl, K_SPMV);
     // graph-driven solve: no further iteration unless sweep 3 or the restart
     // asks for one
-    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ctl->h_loop, 0u);
+    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) {
+        cudaGraphSetConditional(ctl->h_loop, 0u);
+        if (ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 0u);
+    }
     const Item it = items[blockIdx.x];
     SysState<T>* st = sts + it.sys;
     if (st->phase != PH_ARNOLDI) return;
@@ -1124,7 +1128,10 @@ k_dcgs_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     __shared__ T red[SYLV_NWARP][PSTRIDE];
     pdl_wait();
     count_launch(ctl, K_SPMV);
-    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ctl->h_loop, 0u);
+    if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) {
+        cudaGraphSetConditional(ctl->h_loop, 0u);
+        if (ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 0u);
+    }
     const Item it = items[blockIdx.x];
     SysState<T>* st = sts + it.sys;
     if (st->phase != PH_ARNOLDI) return;
