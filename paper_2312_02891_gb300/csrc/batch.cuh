@@ -283,13 +283,18 @@ struct Batch : BatchBase {
             if (tune.chosen > 0) rpc = tune.chosen;
         }
         rpc = (rpc + 31) / 32 * 32;
+        // the outer-step kernels (factor update, Grams, step set-up) touch each
+        // row a few times per outer step: their work items are at least 4096
+        // rows, whatever chunk the inner kernels take (fewer blocks, fewer
+        // chunk partials in the Gram reductions)
+        const int orpc = std::max(rpc, 4096);
         // ---- layout of every instance's buffers in one arena ----
         struct Off { size_t f, g, w, t, Z, Y, gam, hist, alpha, beta, pinvA, pinvB, avalA, avalB, gpart; };
         std::vector<Off> off(count);
         Arena ar;
         for (int i = 0; i < count; ++i) {
             const BatchProb& p = ps[i];
-            const int nchA = (p.n + rpc - 1) / rpc, nchB = (p.m + rpc - 1) / rpc;
+            const int nchA = (p.n + orpc - 1) / orpc, nchB = (p.m + orpc - 1) / orpc;
             Off& q = off[i];
             q.f = ar.take((size_t)p.n * p.r * sizeof(double));
             q.g = ar.take((size_t)p.m * p.r * sizeof(double));
@@ -363,7 +368,7 @@ struct Batch : BatchBase {
             d.avalA = (C*)at(off[i].avalA); d.avalB = (C*)at(off[i].avalB);
             d.sd = eng.d_sd.p + sbase; d.st = eng.d_st.p + sbase; d.ctl = eng.d_ctl.p;
             d.gpart = (T*)at(off[i].gpart);
-            d.nchA = (p.n + rpc - 1) / rpc; d.nchB = (p.m + rpc - 1) / rpc; d.rpc = rpc;
+            d.nchA = (p.n + orpc - 1) / orpc; d.nchB = (p.m + orpc - 1) / orpc; d.rpc = orpc;
             d.s = st.p + i; d.h_done = nullptr;
             for (int b = 0; b < d.nchA + d.nchB; ++b) items.push_back({i, b});
             sbase += 2 * p.r;
@@ -461,8 +466,8 @@ struct Batch : BatchBase {
         void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba));
-            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, ba));
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba, (int)eng.bicg_smem));
+            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, ba, (int)eng.bicg_smem));
             SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_bicg_c<T, S, C>, ngi, bc));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, dcgs_a_smem_bytes<T, S, C>()));

@@ -88,6 +88,156 @@ __device__ __forceinline__ void group_op_row(const SysDesc<T, S, C>& sd, const O
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staging of a work item for the stencil product.  The product
+// at the rows [r0, r1) reads its input vectors at the rows [r0 - H, r1 + H)
+// (H = the largest |offset| of the stored diagonals), its stencil values and
+// (kernel a) the shadow vector at [r0, r1).  Each contiguous range is one TMA
+// bulk copy (cp.async.bulk) into shared memory, all issued at the start of
+// the block and completing on one mbarrier, so a block has its whole input in
+// flight at once instead of one row per thread.  Ranges are widened to
+// 16-byte boundaries (vectors are 32-row aligned); the unaligned ends of the
+// stencil rows are loaded by the threads.  Used when the item fits the
+// launch's dynamic shared memory, otherwise the kernels read global memory
+// directly.
+// ---------------------------------------------------------------------------
+// Dynamic shared memory a staged work item may take: two blocks per SM.
+#define SYLV_BICG_SMEM_CAP (108 * 1024)
+template <typename C> struct StageElems { static constexpr int value = sizeof(C) >= 16 ? 1 : 16 / (int)sizeof(C); };
+template <typename C> HD int stage_ls(int rpc, int halo) {
+    constexpr int e = StageElems<C>::value;
+    return (rpc + 2 * halo + 2 * e + e - 1) / e * e;
+}
+template <typename C> HD int stage_ds(int rpc) {
+    constexpr int e = StageElems<C>::value;
+    return (rpc + 2 * e + e - 1) / e * e;
+}
+template <typename C> HD int stage_hs(int rpc) {
+    constexpr int e = StageElems<C>::value;
+    return (rpc + e - 1) / e * e;
+}
+// Bytes of a staged item: the barrier, nvec neighbour-vector slots and nown
+// own-row slots per active column, one slot per stored diagonal.
+template <typename C> HD size_t stage_bytes(int rpc, int halo, int ndiag, int na, int nvec, int nown) {
+    return 16 + ((size_t)nvec * na * stage_ls<C>(rpc, halo) + (size_t)ndiag * stage_ds<C>(rpc) +
+                 (size_t)nown * na * stage_hs<C>(rpc)) * sizeof(C);
+}
+HD int op_halo_of(const int* offs, int ndiag) {
+    int h = 0;
+    for (int d = 0; d < ndiag; ++d) h = offs[d] < 0 ? (-offs[d] > h ? -offs[d] : h) : (offs[d] > h ? offs[d] : h);
+    return h;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the staged copies; gives up after a bounded number of polls
+// (every thread of the block agrees on the outcome).  On failure the fault is
+// recorded for the host and the caller poisons its partial sums, so the
+// columns end as non-finite instead of the kernel waiting forever.
+__device__ __forceinline__ bool stage_wait(unsigned long long* bar, BatchCtl* ctl) {
+    bool ok = true;
+    for (unsigned it = 0; !mbar_try_wait(bar, 0u); ++it)
+        if (it > (1u << 22)) { ok = false; break; }
+    ok = __syncthreads_and(ok);
+    if (!ok && threadIdx.x == 0) atomicExch(&ctl->stage_fault, 1);
+    return ok;
+}
+
+// Issues the staging of one work item (slot layout: NV neighbour vectors x na
+// active columns of ls elements, ndiag stencil slots of ds, NOWN own-row
+// vector x na of hs).  lo is the first staged neighbour row.
+template <typename T, typename S, typename C, int NV, int NOWN>
+__device__ __forceinline__ void bicg_stage_issue(const SysDesc<T, S, C>& sd, const OpDesc& op, int mask, int r0,
+                                                 int r1, int lo, int hi, const int (&vids)[NV], int own_vid, int ls,
+                                                 int ds, int hs, unsigned char* smem) {
+    constexpr int E = StageElems<C>::value;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem);
+    C* sv = reinterpret_cast<C*>(smem + 16);
+    const int na = __popc(mask);
+    C* sD = sv + (size_t)NV * na * ls;
+    C* sH = sD + (size_t)op.ndiag * ds;
+    const size_t ld = sd.ldv;
+    const size_t cs = (size_t)BV_COUNT * ld;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        // copy lane: neighbour vectors (NV * na), stencil rows (ndiag), own rows (NOWN * na)
+        const void* src = nullptr;
+        void* dst = nullptr;
+        unsigned bytes = 0;
+        if (lane < NV * na) {
+            const int v = lane / na, j = lane % na;
+            int q = 0, c = -1;
+            for (; q < BG_MAXCOL; ++q)
+                if ((mask >> q & 1) && ++c == j) break;
+            src = sd.bv + q * cs + (size_t)vids[v] * ld + lo;
+            dst = sv + ((size_t)v * na + j) * ls;
+            bytes = (unsigned)((hi - lo) * sizeof(C));
+        } else if (lane < NV * na + op.ndiag) {
+            const int d = lane - NV * na;
+            const size_t g0 = (size_t)d * op.n + r0, base = g0 - g0 % E;
+            const size_t a = (g0 + E - 1) / E * E, b = (g0 + (r1 - r0)) / E * E;
+            if (b > a) {
+                src = sd.aval + a;
+                dst = sD + (size_t)d * ds + (a - base);
+                bytes = (unsigned)((b - a) * sizeof(C));
+            }
+        } else if (lane < NV * na + op.ndiag + NOWN * na) {
+            const int j = lane - NV * na - op.ndiag;
+            int q = 0, c = -1;
+            for (; q < BG_MAXCOL; ++q)
+                if ((mask >> q & 1) && ++c == j) break;
+            src = sd.bv + q * cs + (size_t)own_vid * ld + r0;
+            dst = sH + (size_t)j * hs;
+            bytes = (unsigned)(((r1 + E - 1) / E * E - r0) * sizeof(C));
+        }
+        const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+        if (lane == 0) mbar_expect_tx(bar, total);
+        __syncwarp();
+        if (bytes) bulk_to_smem(dst, src, bytes, bar);
+    }
+    // unaligned ends of the stencil rows: plain loads
+    for (int t = threadIdx.x; t < op.ndiag * 2 * E; t += blockDim.x) {
+        const int d = t / (2 * E), u = t % (2 * E);
+        const size_t g0 = (size_t)d * op.n + r0, base = g0 - g0 % E, gend = g0 + (r1 - r0);
+        const size_t a = (g0 + E - 1) / E * E, b = gend / E * E;
+        size_t gi;
+        if (b > a) gi = u < E ? g0 + u : b + (u - E);
+        else gi = g0 + u;
+        const bool in = b > a ? (u < E ? gi < a : gi < gend) : gi < gend;
+        if (in) sD[(size_t)d * ds + (gi - base)] = ldro(sd.aval + gi);
+    }
+}
+
 // Block sums of NV accumulators (warps combined in A, each sum converted to T
 // once) written to out[0..NV).
 template <typename T, typename A, int NV>
@@ -162,21 +312,79 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     C acc[BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = zero<C>();
-    // r, q, rhat and the stencil are not written here: read-only loads
-    auto P = [&](int q, int k) {
-        const C* c = bv + q * cs + (size_t)k;
-        return ldro(c + BV_R * ld) + beta[q] * ldro(c + BV_Q * ld);
-    };
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        C y[BG_MAXCOL];
-        group_op_row(sd, op, sigma, i, mask, P, y);
+    const int rpc = sd.rows_per_chunk;
+    const int halo = op_halo_of(op.offs, op.ndiag);
+    if (sd.aval && stage_bytes<C>(rpc, halo, op.ndiag, na, 2, 1) <= dyn_smem_bytes()) {
+        // staged: r, q at [lo, hi), the stencil rows and rhat in shared memory
+        extern __shared__ __align__(16) unsigned char bsm[];
+        constexpr int E = StageElems<C>::value;
+        const int ls = stage_ls<C>(rpc, halo), ds = stage_ds<C>(rpc), hs = stage_hs<C>(rpc);
+        const int lo = max(0, r0 - halo) / E * E;
+        const int hi = (int)min((size_t)ld, (size_t)((min(sd.n, r1 + halo) + E - 1) / E * E));
+        const int vids[2] = {BV_R, BV_Q};
+        bicg_stage_issue<T, S, C, 2, 1>(sd, op, mask, r0, r1, lo, hi, vids, BV_RH, ls, ds, hs, bsm);
+        const bool ok = stage_wait(reinterpret_cast<unsigned long long*>(bsm), ctl);
+        const C* sR = reinterpret_cast<const C*>(bsm + 16);
+        const C* sQ = sR + (size_t)na * ls;
+        const C* sD = sR + (size_t)2 * na * ls;
+        const C* sH = sD + (size_t)op.ndiag * ds;
+        int slot[BG_MAXCOL];
 #pragma unroll
-        for (int q = 0; q < BG_MAXCOL; ++q) {
-            if (mask >> q & 1) {
-                C* c = bv + q * cs + (size_t)i;
-                c[BV_P * ld] = P(q, i);
-                c[BV_V * ld] = y[q];
-                acc[q] += cmul(ldro(c + BV_RH * ld), y[q]);
+        for (int q = 0; q < BG_MAXCOL; ++q) slot[q] = __popc(mask & ((1 << q) - 1));
+        int dsh[SYLV_MAXDIAG];
+#pragma unroll
+        for (int d = 0; d < SYLV_MAXDIAG; ++d)
+            dsh[d] = d < op.ndiag ? d * ds + (int)(((size_t)d * op.n + r0) % E) - r0 : 0;
+        for (int i = r0 + threadIdx.x; ok && i < r1; i += blockDim.x) {
+            C y[BG_MAXCOL];
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) y[q] = zero<C>();
+#pragma unroll
+            for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+                if (d < op.ndiag) {
+                    const int k = i + op.offs[d];
+                    if (k >= 0 && k < sd.n) {
+                        const C a = sD[dsh[d] + i];
+#pragma unroll
+                        for (int q = 0; q < BG_MAXCOL; ++q)
+                            if (mask >> q & 1) {
+                                const size_t o = (size_t)slot[q] * ls + (k - lo);
+                                y[q] += a * (sR[o] + beta[q] * sQ[o]);
+                            }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) {
+                if (mask >> q & 1) {
+                    const size_t o = (size_t)slot[q] * ls + (i - lo);
+                    C* c = bv + q * cs + (size_t)i;
+                    c[BV_P * ld] = sR[o] + beta[q] * sQ[o];
+                    c[BV_V * ld] = y[q];
+                    acc[q] += cmul(sH[(size_t)slot[q] * hs + (i - r0)], y[q]);
+                }
+            }
+        }
+        if (!ok)
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = from_real<C>((typename RealOf<C>::type)NAN);
+    } else {
+        // r, q, rhat and the stencil are not written here: read-only loads
+        auto P = [&](int q, int k) {
+            const C* c = bv + q * cs + (size_t)k;
+            return ldro(c + BV_R * ld) + beta[q] * ldro(c + BV_Q * ld);
+        };
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            C y[BG_MAXCOL];
+            group_op_row(sd, op, sigma, i, mask, P, y);
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) {
+                if (mask >> q & 1) {
+                    C* c = bv + q * cs + (size_t)i;
+                    c[BV_P * ld] = P(q, i);
+                    c[BV_V * ld] = y[q];
+                    acc[q] += cmul(ldro(c + BV_RH * ld), y[q]);
+                }
             }
         }
     }
@@ -233,22 +441,80 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     C acc[3 * BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = zero<C>();
-    // r, v and the stencil are not written here: read-only loads
-    auto Sf = [&](int q, int k) {
-        const C* c = bv + q * cs + (size_t)k;
-        return ldro(c + BV_R * ld) - alpha[q] * ldro(c + BV_V * ld);
-    };
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        C y[BG_MAXCOL];
-        group_op_row(sd, op, sigma, i, mask, Sf, y);
+    const int rpc = sd.rows_per_chunk;
+    const int halo = op_halo_of(op.offs, op.ndiag);
+    if (sd.aval && stage_bytes<C>(rpc, halo, op.ndiag, na, 2, 0) <= dyn_smem_bytes()) {
+        // staged: r, v at [lo, hi) and the stencil rows in shared memory
+        extern __shared__ __align__(16) unsigned char bsm[];
+        constexpr int E = StageElems<C>::value;
+        const int ls = stage_ls<C>(rpc, halo), ds = stage_ds<C>(rpc);
+        const int lo = max(0, r0 - halo) / E * E;
+        const int hi = (int)min((size_t)ld, (size_t)((min(sd.n, r1 + halo) + E - 1) / E * E));
+        const int vids[2] = {BV_R, BV_V};
+        bicg_stage_issue<T, S, C, 2, 0>(sd, op, mask, r0, r1, lo, hi, vids, 0, ls, ds, 0, bsm);
+        const bool ok = stage_wait(reinterpret_cast<unsigned long long*>(bsm), ctl);
+        const C* sR = reinterpret_cast<const C*>(bsm + 16);
+        const C* sV = sR + (size_t)na * ls;
+        const C* sD = sR + (size_t)2 * na * ls;
+        int slot[BG_MAXCOL];
 #pragma unroll
-        for (int q = 0; q < BG_MAXCOL; ++q) {
-            if (mask >> q & 1) {
-                const C si = Sf(q, i);
-                bv[q * cs + (size_t)BV_T * ld + i] = y[q];
-                acc[3 * q] += cmul(y[q], si);
-                acc[3 * q + 1] += from_real<C>(abs2(y[q]));
-                acc[3 * q + 2] += from_real<C>(abs2(si));
+        for (int q = 0; q < BG_MAXCOL; ++q) slot[q] = __popc(mask & ((1 << q) - 1));
+        int dsh[SYLV_MAXDIAG];
+#pragma unroll
+        for (int d = 0; d < SYLV_MAXDIAG; ++d)
+            dsh[d] = d < op.ndiag ? d * ds + (int)(((size_t)d * op.n + r0) % E) - r0 : 0;
+        for (int i = r0 + threadIdx.x; ok && i < r1; i += blockDim.x) {
+            C y[BG_MAXCOL];
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) y[q] = zero<C>();
+#pragma unroll
+            for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+                if (d < op.ndiag) {
+                    const int k = i + op.offs[d];
+                    if (k >= 0 && k < sd.n) {
+                        const C a = sD[dsh[d] + i];
+#pragma unroll
+                        for (int q = 0; q < BG_MAXCOL; ++q)
+                            if (mask >> q & 1) {
+                                const size_t o = (size_t)slot[q] * ls + (k - lo);
+                                y[q] += a * (sR[o] - alpha[q] * sV[o]);
+                            }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) {
+                if (mask >> q & 1) {
+                    const size_t o = (size_t)slot[q] * ls + (i - lo);
+                    const C si = sR[o] - alpha[q] * sV[o];
+                    bv[q * cs + (size_t)BV_T * ld + i] = y[q];
+                    acc[3 * q] += cmul(y[q], si);
+                    acc[3 * q + 1] += from_real<C>(abs2(y[q]));
+                    acc[3 * q + 2] += from_real<C>(abs2(si));
+                }
+            }
+        }
+        if (!ok)
+#pragma unroll
+            for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = from_real<C>((typename RealOf<C>::type)NAN);
+    } else {
+        // r, v and the stencil are not written here: read-only loads
+        auto Sf = [&](int q, int k) {
+            const C* c = bv + q * cs + (size_t)k;
+            return ldro(c + BV_R * ld) - alpha[q] * ldro(c + BV_V * ld);
+        };
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            C y[BG_MAXCOL];
+            group_op_row(sd, op, sigma, i, mask, Sf, y);
+#pragma unroll
+            for (int q = 0; q < BG_MAXCOL; ++q) {
+                if (mask >> q & 1) {
+                    const C si = Sf(q, i);
+                    bv[q * cs + (size_t)BV_T * ld + i] = y[q];
+                    acc[3 * q] += cmul(y[q], si);
+                    acc[3 * q + 1] += from_real<C>(abs2(y[q]));
+                    acc[3 * q + 2] += from_real<C>(abs2(si));
+                }
             }
         }
     }

@@ -396,6 +396,7 @@ struct BatchCtl {
     // the first inner kernel of every device iteration
     int bouter;             // 1 when h_bouter belongs to the running graph
     cudaGraphConditionalHandle h_bouter;
+    int stage_fault;        // a shared-memory staging wait gave up (the affected columns end non-finite)
 };
 
 __device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {

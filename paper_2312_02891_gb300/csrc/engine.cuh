@@ -179,6 +179,9 @@ struct Engine {
     Dev<C> d_bv;
     Dev<T> d_gpart;
     Dev<unsigned> d_gcount;
+    // dynamic shared memory of k_bicg_a / k_bicg_b: the largest staged work
+    // item (0: every item reads global memory directly)
+    size_t bicg_smem = 0;
     int restart_every = 1;              // host driver: restart kernels every k-th device iteration
     double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
     long long samples[K_COUNT] = {};    // sampled launches
@@ -295,6 +298,22 @@ struct Engine {
             SYLV_TRY(d_gitems.alloc(gitems.size()));
             SYLV_CK(cudaMemcpy(d_groups.p, h_groups.data(), ngroups * sizeof(BGroup<T>), cudaMemcpyHostToDevice));
             SYLV_CK(cudaMemcpy(d_gitems.p, gitems.data(), gitems.size() * sizeof(Item), cudaMemcpyHostToDevice));
+            // staging of the stencil product in shared memory: the largest item
+            // that still leaves room for two blocks per SM
+            bicg_smem = 0;
+            for (const BGroup<T>& bg : h_groups) {
+                const SysDesc<T, S, C>& d0 = h_sd[bg.sys0];
+                if (!d0.aval) continue;
+                const OpDesc& od = ops[d0.op];
+                const size_t b = stage_bytes<C>(rpc, op_halo_of(od.offs, od.ndiag), od.ndiag, bg.ncol, 2, 1);
+                if (b <= SYLV_BICG_SMEM_CAP) bicg_smem = std::max(bicg_smem, b);
+            }
+            if (bicg_smem) {
+                SYLV_CK(cudaFuncSetAttribute(k_bicg_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bicg_smem));
+                SYLV_CK(cudaFuncSetAttribute(k_bicg_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bicg_smem));
+            }
         }
         SYLV_TRY(d_sd.alloc(nsys));
         SYLV_TRY(d_st.alloc(nsys));
@@ -365,9 +384,11 @@ struct Engine {
         };
         if (inner == 1) {
             const dim3 g(ngitems);
-            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, 0, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, bicg_smem, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+                            d_ctl.p));
             SYLV_TRY(mark(K_SPMV));
-            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, 0, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, bicg_smem, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+                            d_ctl.p));
             SYLV_TRY(mark(K_CGS2));
             SYLV_TRY(launch(k_bicg_c<T, S, C>, g, 0, d_sd.p, d_st.p, d_groups.p, d_gitems.p, d_ctl.p));
             SYLV_TRY(mark(K_CGS3));
@@ -535,7 +556,7 @@ int autotune_rpc(const std::vector<int>& sys_n, const std::vector<int>& sys_op, 
     }
     const int nmax = *std::max_element(sys_n.begin(), sys_n.end());
     std::vector<int> cand{(auto_rpc + 31) / 32 * 32};
-    for (int c : {512, 1024, 2048, 4096, 8192})
+    for (int c : {512, 768, 1024, 1536, 2048, 4096, 8192})
         if (c <= std::max(nmax, 256) && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
     // synthetic stencil values for every operator that has pre-scaled diagonals
     std::vector<Dev<C>> tav(aval.size());
@@ -1138,8 +1159,10 @@ struct Adi : AdiBase {
         void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba));
-            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, ba));
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba,
+                                (int)eng.bicg_smem));
+            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, ba,
+                                (int)eng.bicg_smem));
             SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_bicg_c<T, S, C>, ngi, SYLV_BLOCK, bc));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5,
