@@ -8,7 +8,8 @@ the per-step controller history, inner iteration totals, the computed and
 true relative residuals, and a two-sided sketch S = P^T X Q of the factored
 solution (P: n x 16, Q: m x 16 seeded Gaussian, streams 5 and 6).
 ``python tests/golden/make_golden.py batch64 nobl_mid bicgstab`` writes the
-same per instance of the 64-instance batched workload (8 x 8 sketches).
+same per instance of the 64-instance batched workload (8 x 8 sketches, and the
+shifts each instance was solved with).
 """
 from __future__ import annotations
 
@@ -82,8 +83,13 @@ def _batch_one(i, strategy, inner):
     P = np.stack([W.normal(12345, 5, c, p.A.n) for c in range(BATCH_SKETCH)], axis=1)
     Q = np.stack([W.normal(12345, 6, c, p.B.n) for c in range(BATCH_SKETCH)], axis=1)
     S = sketch(res.Z, res.gamma, res.Y, P, Q)
+    # the shifts are stored with the run: the generator's selection compares
+    # bounds of nearly equal candidate sets, so another BLAS/LAPACK can pick
+    # another set, and the parity test must solve with the shifts used here
     return dict(instance=i, n=p.A.n, m=p.B.n, r=p.r, steps=res.steps, converged=bool(res.converged),
                 res_comp=res.res_comp, res_true=tr, inner_its=res.inner_its_A + res.inner_its_B,
+                alpha=[[float(np.real(a)), float(np.imag(a))] for a in p.alpha],
+                beta=[[float(np.real(b)), float(np.imag(b))] for b in p.beta],
                 sketch=np.real(S).tolist(), oracle_wall_s=wall)
 
 

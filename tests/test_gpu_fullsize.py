@@ -7,6 +7,7 @@ tests/golden/make_golden.py, which runs only the oracle.  The solution is
 compared through a two-sided Gaussian sketch P^T X Q (16 x 16, seeded) formed
 from the factors, and the true residual of the GPU factors is evaluated by the
 oracle's exact factored norm."""
+import dataclasses
 import importlib.util
 import json
 import os
@@ -33,6 +34,12 @@ def _golden_module():
 def golden(name):
     with open(os.path.join(HERE, "golden", name + ".json")) as fh:
         return json.load(fh)
+
+
+def stored_shifts(pairs):
+    """Shifts stored as [re, im] pairs; real when every imaginary part is 0."""
+    z = np.array([complex(a, b) for a, b in pairs])
+    return z.real.copy() if not np.any(z.imag) else z
 
 
 @pytest.fixture(scope="module")
@@ -146,9 +153,15 @@ def test_batch64_matches_stored_oracle_runs(batch64, opts):
     g = golden("batch64_nobl_mid_bicgstab")
     ng = g["sketch_cols"]
     worst = 0.0
-    with P.SylvesterADIBatch(batch64, strategy="nobl_mid", jacobi=1, **opts) as bt:
+    # solve with the shifts of the stored runs: the generator's choice between
+    # nearly equal shift sets can differ with the host's BLAS/LAPACK
+    probs = [dataclasses.replace(p, alpha=stored_shifts(gi["alpha"]), beta=stored_shifts(gi["beta"]))
+             for p, gi in zip(batch64, g["instances"])]
+    moved = sum(not np.array_equal(p.alpha, q.alpha) or not np.array_equal(p.beta, q.beta)
+                for p, q in zip(batch64, probs))
+    with P.SylvesterADIBatch(probs, strategy="nobl_mid", jacobi=1, **opts) as bt:
         assert bt.solve() == 0, P.sylv_last_error()
-        for p, gi in zip(batch64, g["instances"]):
+        for p, gi in zip(probs, g["instances"]):
             i = gi["instance"]
             info = bt.info(i)
             assert (p.A.n, p.B.n, p.r) == (gi["n"], gi["m"], gi["r"])
@@ -167,4 +180,5 @@ def test_batch64_matches_stored_oracle_runs(batch64, opts):
             rel = np.linalg.norm(S - Sg) / np.linalg.norm(Sg)
             worst = max(worst, rel)
             assert rel <= 1e-3, (i, rel)
-    print("batch64 %s: largest relative sketch difference %.2e" % (opts, worst))
+    print("batch64 %s: largest relative sketch difference %.2e; %d instances with shifts other than "
+          "this host's generator gives" % (opts, worst, moved))
