@@ -462,12 +462,14 @@ struct Batch : BatchBase {
         auto* grp = eng.d_groups.p;
         auto* gip = eng.d_gitems.p;
         int ngi = eng.ngitems;
-        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &ctp};
+        int sma = eng.bicg_smem[0], smb = eng.bicg_smem[1];
+        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &sma, &ctp};
+        void* bb[] = {&sdp, &stp, &opp, &grp, &gip, &smb, &ctp};
         void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba, (int)eng.bicg_smem));
-            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, ba, (int)eng.bicg_smem));
+            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba, sma));
+            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, bb, smb));
             SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_bicg_c<T, S, C>, ngi, bc));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, dcgs_a_smem_bytes<T, S, C>()));

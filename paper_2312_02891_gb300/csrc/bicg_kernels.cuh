@@ -29,25 +29,26 @@ namespace sylv {
 
 constexpr int BG_MAXCOL = 4;                     // columns of a group (the rank cap)
 constexpr int BG_PSTRIDE = 3 * BG_MAXCOL;        // partial sums per chunk (at most 3 per column)
-// Resident blocks per SM the step kernels are compiled for: they stream a
-// few vectors per row and need many loads in flight, so occupancy comes
-// before registers (the counts keep the stencil path of the product free of
-// spills for each type).
-template <typename C> struct BicgOcc { static constexpr int value = 3; };
-template <> struct BicgOcc<float> { static constexpr int value = 4; };
-template <> struct BicgOcc<cplx> { static constexpr int value = 2; };
 
 // Vectors of one BiCGstab system, column-major, ldv apart, C precision.
 enum BVec : int { BV_R = 0, BV_Q = 1, BV_P = 2, BV_V = 3, BV_T = 4, BV_RH = 5, BV_COUNT = 6 };
 
 // A group: systems sys0 .. sys0 + ncol - 1 (same operator, shift and rows;
 // their vectors lie BV_COUNT * ldv apart), its chunk partial sums and its
-// completion counter.
-template <typename T>
+// completion counter, with copies of the systems' shared descriptor fields
+// (one load resolves a work item).
+template <typename T, typename C>
 struct BGroup {
     int sys0, ncol, nchunks;
     T* part;                 // nchunks x BG_PSTRIDE
     unsigned* counter;
+    int n, rpc, ndiag, halo; // rows, rows per chunk, stored diagonals, largest |offset|
+    size_t ldv;
+    C* bv;                   // vectors of the group's first column
+    const C* aval;           // pre-scaled stencil (null: not stored by diagonals)
+    const T* pinv;           // Jacobi inverse or null
+    int offs[SYLV_MAXDIAG];
+    double nnz;              // nonzeros of the operator (byte counts)
 };
 
 template <typename C> HD C from_real(typename RealOf<C>::type x) { return make_scalar<C>((double)x, 0.0); }
@@ -89,39 +90,48 @@ __device__ __forceinline__ void group_op_row(const SysDesc<T, S, C>& sd, const O
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory staging of a work item for the stencil product.  The product
-// at the rows [r0, r1) reads its input vectors at the rows [r0 - H, r1 + H)
-// (H = the largest |offset| of the stored diagonals), its stencil values and
-// (kernel a) the shadow vector at [r0, r1).  Each contiguous range is one TMA
-// bulk copy (cp.async.bulk) into shared memory, all issued at the start of
-// the block and completing on one mbarrier, so a block has its whole input in
-// flight at once instead of one row per thread.  Ranges are widened to
-// 16-byte boundaries (vectors are 32-row aligned); the unaligned ends of the
-// stencil rows are loaded by the threads.  Used when the item fits the
-// launch's dynamic shared memory, otherwise the kernels read global memory
-// directly.
+// Shared-memory staging of a work item for the stencil product (kernels a
+// and b).  The block's item [r0, r1) of a group is copied into shared memory
+// with TMA bulk copies (cp.async.bulk, issued by the lanes of warp 0, all
+// completing on one mbarrier):
+//   * the two input vectors of each active column at the neighbour rows
+//     [lo, hi) = [r0 - H, r1 + H) rounded out to 16-byte boundaries (H = the
+//     largest |offset| of the stored diagonals); rows outside [0, ldv) are
+//     zero-filled by warp 0, rows in [n, ldv) are zero in global memory (never
+//     written), and the pre-scaled stencil value of a neighbour outside the
+//     grid is zero, so the product needs no bounds checks;
+//   * the stencil diagonals at the own rows (they may start off a 16-byte
+//     boundary: the aligned interior by one bulk copy, the ends by the lane,
+//     the value of row i at shift + (i - r0) in the diagonal's slot);
+//   * (kernel a) the shadow vector at the own rows.
+// Shared-memory indices are 32-bit and the loops over diagonals and columns
+// run to the item's counts.  An item that does not fit the launch's stage
+// size (or an operator that is not a stencil) reads global memory directly.
 // ---------------------------------------------------------------------------
+template <typename X> struct StageElems { static constexpr int value = sizeof(X) >= 16 ? 1 : 16 / (int)sizeof(X); };
+template <typename X> HD int round_e(int k) {
+    constexpr int e = StageElems<X>::value;
+    return (k + e - 1) / e * e;
+}
+// slot lengths (elements; every slot is a multiple of 16 bytes)
+template <typename X> HD int slot_nb(int rpc, int halo) {
+    return round_e<X>(rpc + 2 * halo + 2 * StageElems<X>::value);
+}
+template <typename X> HD int slot_ow(int rpc) { return round_e<X>(rpc); }
+template <typename X> HD int slot_sh(int rpc) { return round_e<X>(rpc + StageElems<X>::value); }
+// bytes of a staged item with na active columns: kernel a (r, q at the
+// neighbours, the stencil, rhat), kernel b (r, v at the neighbours, the
+// stencil)
+template <typename C> HD size_t stage_bytes_a(int rpc, int halo, int ndiag, int na) {
+    return ((size_t)2 * na * slot_nb<C>(rpc, halo) + (size_t)ndiag * slot_sh<C>(rpc) + (size_t)na * slot_ow<C>(rpc)) *
+           sizeof(C);
+}
+template <typename C> HD size_t stage_bytes_b(int rpc, int halo, int ndiag, int na) {
+    return ((size_t)2 * na * slot_nb<C>(rpc, halo) + (size_t)ndiag * slot_sh<C>(rpc)) * sizeof(C);
+}
 // Dynamic shared memory a staged work item may take: two blocks per SM.
 #define SYLV_BICG_SMEM_CAP (108 * 1024)
-template <typename C> struct StageElems { static constexpr int value = sizeof(C) >= 16 ? 1 : 16 / (int)sizeof(C); };
-template <typename C> HD int stage_ls(int rpc, int halo) {
-    constexpr int e = StageElems<C>::value;
-    return (rpc + 2 * halo + 2 * e + e - 1) / e * e;
-}
-template <typename C> HD int stage_ds(int rpc) {
-    constexpr int e = StageElems<C>::value;
-    return (rpc + 2 * e + e - 1) / e * e;
-}
-template <typename C> HD int stage_hs(int rpc) {
-    constexpr int e = StageElems<C>::value;
-    return (rpc + e - 1) / e * e;
-}
-// Bytes of a staged item: the barrier, nvec neighbour-vector slots and nown
-// own-row slots per active column, one slot per stored diagonal.
-template <typename C> HD size_t stage_bytes(int rpc, int halo, int ndiag, int na, int nvec, int nown) {
-    return 16 + ((size_t)nvec * na * stage_ls<C>(rpc, halo) + (size_t)ndiag * stage_ds<C>(rpc) +
-                 (size_t)nown * na * stage_hs<C>(rpc)) * sizeof(C);
-}
+
 HD int op_halo_of(const int* offs, int ndiag) {
     int h = 0;
     for (int d = 0; d < ndiag; ++d) h = offs[d] < 0 ? (-offs[d] > h ? -offs[d] : h) : (offs[d] > h ? offs[d] : h);
@@ -129,16 +139,14 @@ HD int op_halo_of(const int* offs, int ndiag) {
 }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned dyn_smem_bytes() {
-    unsigned v;
-    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
-    return v;
-}
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+// arrival with the bytes the bulk copies will complete (release: warp 0's
+// generic stores into the stage are visible to a thread that sees the phase
+// complete)
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
@@ -160,86 +168,134 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 // Waits for the staged copies; gives up after a bounded number of polls
 // (every thread of the block agrees on the outcome).  On failure the fault is
-// recorded for the host and the caller poisons its partial sums, so the
-// columns end as non-finite instead of the kernel waiting forever.
+// recorded for the host, the block waits once more (again bounded) for its
+// copies in flight, and the caller poisons its partial sums, so the columns
+// end as non-finite instead of the kernel waiting forever.
 __device__ __forceinline__ bool stage_wait(unsigned long long* bar, BatchCtl* ctl) {
     bool ok = true;
     for (unsigned it = 0; !mbar_try_wait(bar, 0u); ++it)
         if (it > (1u << 22)) { ok = false; break; }
     ok = __syncthreads_and(ok);
-    if (!ok && threadIdx.x == 0) atomicExch(&ctl->stage_fault, 1);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(&ctl->stage_fault, 1);
+        for (unsigned it = 0; !mbar_try_wait(bar, 0u) && it <= (1u << 22); ++it) {
+        }
+        __syncthreads();
+    }
     return ok;
 }
 
-// Issues the staging of one work item (slot layout: NV neighbour vectors x na
-// active columns of ls elements, ndiag stencil slots of ds, NOWN own-row
-// vector x na of hs).  lo is the first staged neighbour row.
-template <typename T, typename S, typename C, int NV, int NOWN>
-__device__ __forceinline__ void bicg_stage_issue(const SysDesc<T, S, C>& sd, const OpDesc& op, int mask, int r0,
-                                                 int r1, int lo, int hi, const int (&vids)[NV], int own_vid, int ls,
-                                                 int ds, int hs, unsigned char* smem) {
-    constexpr int E = StageElems<C>::value;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem);
-    C* sv = reinterpret_cast<C*>(smem + 16);
-    const int na = __popc(mask);
-    C* sD = sv + (size_t)NV * na * ls;
-    C* sH = sD + (size_t)op.ndiag * ds;
-    const size_t ld = sd.ldv;
-    const size_t cs = (size_t)BV_COUNT * ld;
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        // copy lane: neighbour vectors (NV * na), stencil rows (ndiag), own rows (NOWN * na)
-        const void* src = nullptr;
-        void* dst = nullptr;
-        unsigned bytes = 0;
-        if (lane < NV * na) {
-            const int v = lane / na, j = lane % na;
-            int q = 0, c = -1;
-            for (; q < BG_MAXCOL; ++q)
-                if ((mask >> q & 1) && ++c == j) break;
-            src = sd.bv + q * cs + (size_t)vids[v] * ld + lo;
-            dst = sv + ((size_t)v * na + j) * ls;
-            bytes = (unsigned)((hi - lo) * sizeof(C));
-        } else if (lane < NV * na + op.ndiag) {
-            const int d = lane - NV * na;
-            const size_t g0 = (size_t)d * op.n + r0, base = g0 - g0 % E;
-            const size_t a = (g0 + E - 1) / E * E, b = (g0 + (r1 - r0)) / E * E;
-            if (b > a) {
-                src = sd.aval + a;
-                dst = sD + (size_t)d * ds + (a - base);
-                bytes = (unsigned)((b - a) * sizeof(C));
-            }
-        } else if (lane < NV * na + op.ndiag + NOWN * na) {
-            const int j = lane - NV * na - op.ndiag;
-            int q = 0, c = -1;
-            for (; q < BG_MAXCOL; ++q)
-                if ((mask >> q & 1) && ++c == j) break;
-            src = sd.bv + q * cs + (size_t)own_vid * ld + r0;
-            dst = sH + (size_t)j * hs;
-            bytes = (unsigned)(((r1 + E - 1) / E * E - r0) * sizeof(C));
-        }
-        const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
-        if (lane == 0) mbar_expect_tx(bar, total);
-        __syncwarp();
-        if (bytes) bulk_to_smem(dst, src, bytes, bar);
+// Column of active slot j of a column mask.
+__device__ __forceinline__ int col_of(int mask, int j) {
+    int q = 0, c = -1;
+    for (; q < BG_MAXCOL; ++q)
+        if ((mask >> q & 1) && ++c == j) break;
+    return q;
+}
+
+// Own rows [r0, r0 + m) of an array that may start off a 16-byte boundary,
+// copied into the slot at dst so that element e lands at dst[shift + e]
+// (shift = the array's offset from the 16-byte boundary below it, in
+// elements): the aligned interior by one bulk copy, the rest by the lane.
+template <typename X>
+__device__ __forceinline__ int sh_shift(const X* src) { return (int)(((uintptr_t)src & 15) / sizeof(X)); }
+template <typename X>
+__device__ __forceinline__ void sh_plan(const X* src, int m, X* dst, const void*& csrc, void*& cdst, unsigned& bytes) {
+    const uintptr_t s0 = (uintptr_t)src, s1 = s0 + (uintptr_t)m * sizeof(X);
+    const uintptr_t a = (s0 + 15) & ~(uintptr_t)15, b = s1 & ~(uintptr_t)15;
+    if (b > a) {
+        csrc = reinterpret_cast<const void*>(a);
+        cdst = reinterpret_cast<unsigned char*>(dst) + (a - (s0 & ~(uintptr_t)15));
+        bytes = (unsigned)(b - a);
     }
-    // unaligned ends of the stencil rows: plain loads
-    for (int t = threadIdx.x; t < op.ndiag * 2 * E; t += blockDim.x) {
-        const int d = t / (2 * E), u = t % (2 * E);
-        const size_t g0 = (size_t)d * op.n + r0, base = g0 - g0 % E, gend = g0 + (r1 - r0);
-        const size_t a = (g0 + E - 1) / E * E, b = gend / E * E;
-        size_t gi;
-        if (b > a) gi = u < E ? g0 + u : b + (u - E);
-        else gi = g0 + u;
-        const bool in = b > a ? (u < E ? gi < a : gi < gend) : gi < gend;
-        if (in) sD[(size_t)d * ds + (gi - base)] = ldro(sd.aval + gi);
+    const int shift = sh_shift(src);
+    for (int e = 0; e < m; ++e) {
+        const uintptr_t p = s0 + (uintptr_t)e * sizeof(X);
+        if (b > a && p >= a && p < b) {
+            e += (int)((b - p) / sizeof(X)) - 1;
+            continue;
+        }
+        dst[shift + e] = ldro(src + e);
     }
 }
 
-// Block sums of NV accumulators (warps combined in A, each sum converted to T
-// once) written to out[0..NV).
+// Warp 0: issues the staging of the block's item.  KIND 0: kernel a (r and
+// q at the neighbours, the stencil, rhat), 1: kernel b (r and v at the
+// neighbours, the stencil).  Slot order: neighbour vectors v * na + j, the
+// ndiag diagonals, (a) rhat of slot j.
+template <typename T, typename C, int KIND>
+__device__ __forceinline__ void bicg_stage_issue(const BGroup<T, C>& g, int mask, int na, int r0, int r1, int lo,
+                                                 int hi, unsigned char* smem, unsigned long long* bar) {
+    const int lane = threadIdx.x & 31;
+    const size_t ld = g.ldv, cs = (size_t)BV_COUNT * ld;
+    const int ls = slot_nb<C>(g.rpc, g.halo), ds = slot_sh<C>(g.rpc);
+    C* const sc = reinterpret_cast<C*>(smem);
+    const void* csrc = nullptr;
+    void* cdst = nullptr;
+    unsigned bytes = 0;
+    int u = lane;
+    if (u < 2 * na) {
+        const int v = u / na, j = u % na;
+        const int vid = v == 0 ? BV_R : (KIND == 0 ? BV_Q : BV_V);
+        const int a0 = max(lo, 0), a1 = (int)min((size_t)hi, ld);
+        if (a1 > a0) {
+            csrc = g.bv + col_of(mask, j) * cs + (size_t)vid * ld + a0;
+            cdst = sc + (size_t)u * ls + (a0 - lo);
+            bytes = (unsigned)((a1 - a0) * sizeof(C));
+        }
+    } else if ((u -= 2 * na) < g.ndiag) {
+        sh_plan(g.aval + (size_t)u * g.n + r0, r1 - r0, sc + (size_t)2 * na * ls + (size_t)u * ds, csrc, cdst, bytes);
+    } else if (KIND == 0 && (u -= g.ndiag) < na) {
+        csrc = g.bv + col_of(mask, u) * cs + (size_t)BV_RH * ld + r0;
+        cdst = sc + (size_t)2 * na * ls + (size_t)g.ndiag * ds + (size_t)u * slot_ow<C>(g.rpc);
+        bytes = (unsigned)(round_e<C>(r1 - r0) * sizeof(C));
+    }
+    // rows of the neighbour ranges outside [0, ldv): zero
+    const int z0 = max(0, -lo), z1 = (int)max((long long)0, (long long)hi - (long long)ld);
+    if (z0 || z1) {
+        for (int v = 0; v < 2 * na; ++v) {
+            C* s = sc + (size_t)v * ls;
+            for (int e = lane; e < z0; e += 32) s[e] = zero<C>();
+            for (int e = lane; e < z1; e += 32) s[(int)(ld - lo) + e] = zero<C>();
+        }
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+    __syncwarp();
+    if (lane == 0) mbar_arrive_tx(bar, total);
+    __syncwarp();
+    if (bytes) bulk_to_smem(cdst, csrc, bytes, bar);
+}
+
+// Block sums of K * BG_MAXCOL accumulators kept per active slot j (warps
+// combined in A, each sum converted to T once), written to
+// out[col[j] * K + k] for the na active slots.
+template <typename T, typename A, int K>
+__device__ __forceinline__ void bg_block_sums_slots(A (&acc)[K * BG_MAXCOL], T* out, const int (&col)[BG_MAXCOL],
+                                                    int na) {
+    __shared__ A red[SYLV_NWARP][K * BG_MAXCOL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int l = 0; l < K * BG_MAXCOL; ++l) {
+        if (l < K * na) {
+            const A v = warp_sum(acc[l]);
+            if (lane == 0) red[warp][l] = v;
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < K * na; l += blockDim.x) {
+        A s = red[0][l];
+#pragma unroll
+        for (int w = 1; w < SYLV_NWARP; ++w) s += red[w][l];
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < BG_MAXCOL; ++j)
+            if (j == l / K) c = col[j];
+        out[c * K + l % K] = cvt<T>(s);
+    }
+}
+
+// Block sums of NV accumulators indexed by column (warps combined in A, each
+// sum converted to T once) written to out[0..NV).
 template <typename T, typename A, int NV>
 __device__ __forceinline__ void bg_block_sums(A (&acc)[NV], T* out) {
     __shared__ A red[SYLV_NWARP][NV];
@@ -259,8 +315,8 @@ __device__ __forceinline__ void bg_block_sums(A (&acc)[NV], T* out) {
 }
 
 // Active columns of a group (phase == ph), as a bit mask.
-template <typename T>
-__device__ __forceinline__ int group_mask(const SysState<T>* sts, const BGroup<T>& g, int ph) {
+template <typename T, typename C>
+__device__ __forceinline__ int group_mask(const SysState<T>* sts, const BGroup<T, C>& g, int ph) {
     int mask = 0;
     for (int q = 0; q < g.ncol; ++q)
         if (sts[g.sys0 + q].phase == ph) mask |= 1 << q;
@@ -280,9 +336,9 @@ __device__ __forceinline__ void bicg_end_cycle(SysState<T>* st) {
 // non-finite denominator ends the cycle (breakdown) without an update.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
+__global__ void __launch_bounds__(SYLV_BLOCK, 3)
 k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
-         const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
+         const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int cap, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_SPMV);
     if (ctl->graph && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -290,88 +346,90 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         if (ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 0u);
     }
     const Item it = items[blockIdx.x];
-    const BGroup<T> g = groups[it.sys];
+    const BGroup<T, C>& g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
     if (!mask) return;
-    const SysDesc<T, S, C> sd = sysd[g.sys0];
-    const OpDesc op = ops[sd.op];
-    const size_t ld = sd.ldv;
-    const int r0 = it.chunk * sd.rows_per_chunk;
-    const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
     const int na = __popc(mask);
-    count_work(ctl, K_SPMV, it.chunk, (double)op.nnz * sizeof(C) + 5.0 * na * sd.n * sizeof(C),
-               FmaFlops<C>::v * na * ((double)op.nnz + 2.0 * sd.n));
-    C beta[BG_MAXCOL];
+    const int r0 = it.chunk * g.rpc, r1 = min(g.n, r0 + g.rpc);
+    count_work(ctl, K_SPMV, it.chunk, g.nnz * sizeof(C) + 5.0 * na * g.n * sizeof(C),
+               FmaFlops<C>::v * na * (g.nnz + 2.0 * g.n));
+    int col[BG_MAXCOL];
 #pragma unroll
-    for (int q = 0; q < BG_MAXCOL; ++q)
-        beta[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].bbeta) : zero<C>();
-    // vector v of column q: bv + (q BV_COUNT + v) ld
-    C* __restrict__ bv = sd.bv;
-    const size_t cs = (size_t)BV_COUNT * ld;
-    const T sigma = sts[g.sys0].sigma;
+    for (int j = 0; j < BG_MAXCOL; ++j) col[j] = j < na ? col_of(mask, j) : 0;
     C acc[BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = zero<C>();
-    const int rpc = sd.rows_per_chunk;
-    const int halo = op_halo_of(op.offs, op.ndiag);
-    if (sd.aval && stage_bytes<C>(rpc, halo, op.ndiag, na, 2, 1) <= dyn_smem_bytes()) {
-        // staged: r, q at [lo, hi), the stencil rows and rhat in shared memory
-        extern __shared__ __align__(16) unsigned char bsm[];
+    const size_t ld = g.ldv, vcs = (size_t)BV_COUNT * ld;
+    if (g.aval && stage_bytes_a<C>(g.rpc, g.halo, g.ndiag, na) <= (size_t)cap) {
+        extern __shared__ __align__(128) unsigned char bsm[];
+        __shared__ __align__(8) unsigned long long bar;
         constexpr int E = StageElems<C>::value;
-        const int ls = stage_ls<C>(rpc, halo), ds = stage_ds<C>(rpc), hs = stage_hs<C>(rpc);
-        const int lo = max(0, r0 - halo) / E * E;
-        const int hi = (int)min((size_t)ld, (size_t)((min(sd.n, r1 + halo) + E - 1) / E * E));
-        const int vids[2] = {BV_R, BV_Q};
-        bicg_stage_issue<T, S, C, 2, 1>(sd, op, mask, r0, r1, lo, hi, vids, BV_RH, ls, ds, hs, bsm);
-        const bool ok = stage_wait(reinterpret_cast<unsigned long long*>(bsm), ctl);
-        const C* sR = reinterpret_cast<const C*>(bsm + 16);
-        const C* sQ = sR + (size_t)na * ls;
-        const C* sD = sR + (size_t)2 * na * ls;
-        const C* sH = sD + (size_t)op.ndiag * ds;
-        int slot[BG_MAXCOL];
+        const int ndiag = g.ndiag, halo = g.halo;
+        const int lo = ((r0 - halo) >= 0 ? (r0 - halo) / E : -((halo - r0 + E - 1) / E)) * E;   // floor to E
+        const int hi = (r1 + halo + E - 1) / E * E;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x < 32) bicg_stage_issue<T, C, 0>(g, mask, na, r0, r1, lo, hi, bsm, &bar);
+        C beta[BG_MAXCOL];
+        C* outc[BG_MAXCOL];
 #pragma unroll
-        for (int q = 0; q < BG_MAXCOL; ++q) slot[q] = __popc(mask & ((1 << q) - 1));
-        int dsh[SYLV_MAXDIAG];
+        for (int j = 0; j < BG_MAXCOL; ++j) {
+            beta[j] = j < na ? cvt<C>(sts[g.sys0 + col[j]].bbeta) : zero<C>();
+            outc[j] = g.bv + col[j] * vcs;
+        }
+        const int ls = slot_nb<C>(g.rpc, halo), ds = slot_sh<C>(g.rpc), hs = slot_ow<C>(g.rpc);
+        int doff[SYLV_MAXDIAG], koff[SYLV_MAXDIAG];
 #pragma unroll
-        for (int d = 0; d < SYLV_MAXDIAG; ++d)
-            dsh[d] = d < op.ndiag ? d * ds + (int)(((size_t)d * op.n + r0) % E) - r0 : 0;
-        for (int i = r0 + threadIdx.x; ok && i < r1; i += blockDim.x) {
+        for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+            doff[d] = d < ndiag ? d * ds + sh_shift(g.aval + (size_t)d * g.n + r0) : 0;
+            koff[d] = d < ndiag ? r0 - lo + g.offs[d] : 0;
+        }
+        const bool ok = stage_wait(&bar, ctl);
+        const C* sR = reinterpret_cast<const C*>(bsm);
+        const C* sQ = sR + na * ls;
+        const C* sD = sR + 2 * na * ls;
+        const C* sH = sD + ndiag * ds;
+        for (int il = threadIdx.x; ok && il < r1 - r0; il += blockDim.x) {
             C y[BG_MAXCOL];
 #pragma unroll
-            for (int q = 0; q < BG_MAXCOL; ++q) y[q] = zero<C>();
+            for (int j = 0; j < BG_MAXCOL; ++j) y[j] = zero<C>();
 #pragma unroll
             for (int d = 0; d < SYLV_MAXDIAG; ++d) {
-                if (d < op.ndiag) {
-                    const int k = i + op.offs[d];
-                    if (k >= 0 && k < sd.n) {
-                        const C a = sD[dsh[d] + i];
+                if (d < ndiag) {
+                    const C a = sD[doff[d] + il];
+                    const int k = il + koff[d];
 #pragma unroll
-                        for (int q = 0; q < BG_MAXCOL; ++q)
-                            if (mask >> q & 1) {
-                                const size_t o = (size_t)slot[q] * ls + (k - lo);
-                                y[q] += a * (sR[o] + beta[q] * sQ[o]);
-                            }
-                    }
+                    for (int j = 0; j < BG_MAXCOL; ++j)
+                        if (j < na) y[j] += a * (sR[j * ls + k] + beta[j] * sQ[j * ls + k]);
                 }
             }
+            const int ko = il + r0 - lo;
 #pragma unroll
-            for (int q = 0; q < BG_MAXCOL; ++q) {
-                if (mask >> q & 1) {
-                    const size_t o = (size_t)slot[q] * ls + (i - lo);
-                    C* c = bv + q * cs + (size_t)i;
-                    c[BV_P * ld] = sR[o] + beta[q] * sQ[o];
-                    c[BV_V * ld] = y[q];
-                    acc[q] += cmul(sH[(size_t)slot[q] * hs + (i - r0)], y[q]);
+            for (int j = 0; j < BG_MAXCOL; ++j) {
+                if (j < na) {
+                    C* c = outc[j] + (size_t)(r0 + il);
+                    c[BV_P * ld] = sR[j * ls + ko] + beta[j] * sQ[j * ls + ko];
+                    c[BV_V * ld] = y[j];
+                    acc[j] += cmul(sH[j * hs + il], y[j]);
                 }
             }
         }
         if (!ok)
 #pragma unroll
             for (int q = 0; q < BG_MAXCOL; ++q) acc[q] = from_real<C>((typename RealOf<C>::type)NAN);
+        bg_block_sums_slots<T, C, 1>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE, col, na);
     } else {
         // r, q, rhat and the stencil are not written here: read-only loads
+        const SysDesc<T, S, C> sd = sysd[g.sys0];
+        const OpDesc op = ops[sd.op];
+        const T sigma = sts[g.sys0].sigma;
+        C beta[BG_MAXCOL];
+#pragma unroll
+        for (int q = 0; q < BG_MAXCOL; ++q)
+            beta[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].bbeta) : zero<C>();
+        C* __restrict__ bv = sd.bv;
         auto P = [&](int q, int k) {
-            const C* c = bv + q * cs + (size_t)k;
+            const C* c = bv + q * vcs + (size_t)k;
             return ldro(c + BV_R * ld) + beta[q] * ldro(c + BV_Q * ld);
         };
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -380,15 +438,15 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 #pragma unroll
             for (int q = 0; q < BG_MAXCOL; ++q) {
                 if (mask >> q & 1) {
-                    C* c = bv + q * cs + (size_t)i;
+                    C* c = bv + q * vcs + (size_t)i;
                     c[BV_P * ld] = P(q, i);
                     c[BV_V * ld] = y[q];
                     acc[q] += cmul(ldro(c + BV_RH * ld), y[q]);
                 }
             }
         }
+        bg_block_sums<T, C, BG_MAXCOL>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE);
     }
-    bg_block_sums<T, C, BG_MAXCOL>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE);
     pdl_trigger();
     if (!last_block(g.counter, g.nchunks)) return;
     __shared__ T tot[BG_PSTRIDE];
@@ -414,93 +472,96 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // when ||s|| already meets the tolerance.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
+__global__ void __launch_bounds__(SYLV_BLOCK, 3)
 k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
-         const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
+         const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int cap, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_CGS2);
     const Item it = items[blockIdx.x];
-    const BGroup<T> g = groups[it.sys];
+    const BGroup<T, C>& g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
     if (!mask) return;
-    const SysDesc<T, S, C> sd = sysd[g.sys0];
-    const OpDesc op = ops[sd.op];
-    const size_t ld = sd.ldv;
-    const int r0 = it.chunk * sd.rows_per_chunk;
-    const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
     const int na = __popc(mask);
-    count_work(ctl, K_CGS2, it.chunk, (double)op.nnz * sizeof(C) + 3.0 * na * sd.n * sizeof(C),
-               FmaFlops<C>::v * na * ((double)op.nnz + 4.0 * sd.n));
-    C alpha[BG_MAXCOL];
+    const int r0 = it.chunk * g.rpc, r1 = min(g.n, r0 + g.rpc);
+    count_work(ctl, K_CGS2, it.chunk, g.nnz * sizeof(C) + 3.0 * na * g.n * sizeof(C),
+               FmaFlops<C>::v * na * (g.nnz + 4.0 * g.n));
+    int col[BG_MAXCOL];
 #pragma unroll
-    for (int q = 0; q < BG_MAXCOL; ++q)
-        alpha[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].balpha) : zero<C>();
-    C* __restrict__ bv = sd.bv;
-    const size_t cs = (size_t)BV_COUNT * ld;
-    const T sigma = sts[g.sys0].sigma;
+    for (int j = 0; j < BG_MAXCOL; ++j) col[j] = j < na ? col_of(mask, j) : 0;
     C acc[3 * BG_MAXCOL];
 #pragma unroll
     for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = zero<C>();
-    const int rpc = sd.rows_per_chunk;
-    const int halo = op_halo_of(op.offs, op.ndiag);
-    if (sd.aval && stage_bytes<C>(rpc, halo, op.ndiag, na, 2, 0) <= dyn_smem_bytes()) {
-        // staged: r, v at [lo, hi) and the stencil rows in shared memory
-        extern __shared__ __align__(16) unsigned char bsm[];
+    const size_t ld = g.ldv, vcs = (size_t)BV_COUNT * ld;
+    if (g.aval && stage_bytes_b<C>(g.rpc, g.halo, g.ndiag, na) <= (size_t)cap) {
+        extern __shared__ __align__(128) unsigned char bsm[];
+        __shared__ __align__(8) unsigned long long bar;
         constexpr int E = StageElems<C>::value;
-        const int ls = stage_ls<C>(rpc, halo), ds = stage_ds<C>(rpc);
-        const int lo = max(0, r0 - halo) / E * E;
-        const int hi = (int)min((size_t)ld, (size_t)((min(sd.n, r1 + halo) + E - 1) / E * E));
-        const int vids[2] = {BV_R, BV_V};
-        bicg_stage_issue<T, S, C, 2, 0>(sd, op, mask, r0, r1, lo, hi, vids, 0, ls, ds, 0, bsm);
-        const bool ok = stage_wait(reinterpret_cast<unsigned long long*>(bsm), ctl);
-        const C* sR = reinterpret_cast<const C*>(bsm + 16);
-        const C* sV = sR + (size_t)na * ls;
-        const C* sD = sR + (size_t)2 * na * ls;
-        int slot[BG_MAXCOL];
+        const int ndiag = g.ndiag, halo = g.halo;
+        const int lo = ((r0 - halo) >= 0 ? (r0 - halo) / E : -((halo - r0 + E - 1) / E)) * E;   // floor to E
+        const int hi = (r1 + halo + E - 1) / E * E;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x < 32) bicg_stage_issue<T, C, 1>(g, mask, na, r0, r1, lo, hi, bsm, &bar);
+        C alpha[BG_MAXCOL];
+        C* outc[BG_MAXCOL];
 #pragma unroll
-        for (int q = 0; q < BG_MAXCOL; ++q) slot[q] = __popc(mask & ((1 << q) - 1));
-        int dsh[SYLV_MAXDIAG];
+        for (int j = 0; j < BG_MAXCOL; ++j) {
+            alpha[j] = j < na ? cvt<C>(sts[g.sys0 + col[j]].balpha) : zero<C>();
+            outc[j] = g.bv + col[j] * vcs + (size_t)BV_T * ld;
+        }
+        const int ls = slot_nb<C>(g.rpc, halo), ds = slot_sh<C>(g.rpc);
+        int doff[SYLV_MAXDIAG], koff[SYLV_MAXDIAG];
 #pragma unroll
-        for (int d = 0; d < SYLV_MAXDIAG; ++d)
-            dsh[d] = d < op.ndiag ? d * ds + (int)(((size_t)d * op.n + r0) % E) - r0 : 0;
-        for (int i = r0 + threadIdx.x; ok && i < r1; i += blockDim.x) {
+        for (int d = 0; d < SYLV_MAXDIAG; ++d) {
+            doff[d] = d < ndiag ? d * ds + sh_shift(g.aval + (size_t)d * g.n + r0) : 0;
+            koff[d] = d < ndiag ? r0 - lo + g.offs[d] : 0;
+        }
+        const bool ok = stage_wait(&bar, ctl);
+        const C* sR = reinterpret_cast<const C*>(bsm);
+        const C* sV = sR + na * ls;
+        const C* sD = sR + 2 * na * ls;
+        for (int il = threadIdx.x; ok && il < r1 - r0; il += blockDim.x) {
             C y[BG_MAXCOL];
 #pragma unroll
-            for (int q = 0; q < BG_MAXCOL; ++q) y[q] = zero<C>();
+            for (int j = 0; j < BG_MAXCOL; ++j) y[j] = zero<C>();
 #pragma unroll
             for (int d = 0; d < SYLV_MAXDIAG; ++d) {
-                if (d < op.ndiag) {
-                    const int k = i + op.offs[d];
-                    if (k >= 0 && k < sd.n) {
-                        const C a = sD[dsh[d] + i];
+                if (d < ndiag) {
+                    const C a = sD[doff[d] + il];
+                    const int k = il + koff[d];
 #pragma unroll
-                        for (int q = 0; q < BG_MAXCOL; ++q)
-                            if (mask >> q & 1) {
-                                const size_t o = (size_t)slot[q] * ls + (k - lo);
-                                y[q] += a * (sR[o] - alpha[q] * sV[o]);
-                            }
-                    }
+                    for (int j = 0; j < BG_MAXCOL; ++j)
+                        if (j < na) y[j] += a * (sR[j * ls + k] - alpha[j] * sV[j * ls + k]);
                 }
             }
+            const int ko = il + r0 - lo;
 #pragma unroll
-            for (int q = 0; q < BG_MAXCOL; ++q) {
-                if (mask >> q & 1) {
-                    const size_t o = (size_t)slot[q] * ls + (i - lo);
-                    const C si = sR[o] - alpha[q] * sV[o];
-                    bv[q * cs + (size_t)BV_T * ld + i] = y[q];
-                    acc[3 * q] += cmul(y[q], si);
-                    acc[3 * q + 1] += from_real<C>(abs2(y[q]));
-                    acc[3 * q + 2] += from_real<C>(abs2(si));
+            for (int j = 0; j < BG_MAXCOL; ++j) {
+                if (j < na) {
+                    const C si = sR[j * ls + ko] - alpha[j] * sV[j * ls + ko];
+                    outc[j][r0 + il] = y[j];
+                    acc[3 * j] += cmul(y[j], si);
+                    acc[3 * j + 1] += from_real<C>(abs2(y[j]));
+                    acc[3 * j + 2] += from_real<C>(abs2(si));
                 }
             }
         }
         if (!ok)
 #pragma unroll
             for (int q = 0; q < 3 * BG_MAXCOL; ++q) acc[q] = from_real<C>((typename RealOf<C>::type)NAN);
+        bg_block_sums_slots<T, C, 3>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE, col, na);
     } else {
         // r, v and the stencil are not written here: read-only loads
+        const SysDesc<T, S, C> sd = sysd[g.sys0];
+        const OpDesc op = ops[sd.op];
+        const T sigma = sts[g.sys0].sigma;
+        C alpha[BG_MAXCOL];
+#pragma unroll
+        for (int q = 0; q < BG_MAXCOL; ++q)
+            alpha[q] = (mask >> q & 1) ? cvt<C>(sts[g.sys0 + q].balpha) : zero<C>();
+        C* __restrict__ bv = sd.bv;
         auto Sf = [&](int q, int k) {
-            const C* c = bv + q * cs + (size_t)k;
+            const C* c = bv + q * vcs + (size_t)k;
             return ldro(c + BV_R * ld) - alpha[q] * ldro(c + BV_V * ld);
         };
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -510,15 +571,15 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
             for (int q = 0; q < BG_MAXCOL; ++q) {
                 if (mask >> q & 1) {
                     const C si = Sf(q, i);
-                    bv[q * cs + (size_t)BV_T * ld + i] = y[q];
+                    bv[q * vcs + (size_t)BV_T * ld + i] = y[q];
                     acc[3 * q] += cmul(y[q], si);
                     acc[3 * q + 1] += from_real<C>(abs2(y[q]));
                     acc[3 * q + 2] += from_real<C>(abs2(si));
                 }
             }
         }
+        bg_block_sums<T, C, 3 * BG_MAXCOL>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE);
     }
-    bg_block_sums<T, C, 3 * BG_MAXCOL>(acc, g.part + (size_t)it.chunk * BG_PSTRIDE);
     pdl_trigger();
     if (!last_block(g.counter, g.nchunks)) return;
     __shared__ T tot[BG_PSTRIDE];
@@ -537,9 +598,9 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
             const T om = tt > 0.0 ? ts * (1.0 / tt) : zero<T>();
             // a non-finite omega ends the step like a converged s (omega = 0,
             // x += alpha P^{-1} p); the restart then checks the true residual
-            const bool ok = isfinite(absv(om));
-            st->bomega = ok ? om : zero<T>();
-            st->bfin = ok ? 0 : 1;
+            const bool okw = isfinite(absv(om));
+            st->bomega = okw ? om : zero<T>();
+            st->bfin = okw ? 0 : 1;
             st->est = sn;
         }
     }
@@ -554,23 +615,20 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // beta' = (rho' / rho)(alpha / omega).
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, BicgOcc<C>::value)
+__global__ void __launch_bounds__(SYLV_BLOCK, 4)
 k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
-         const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
+         const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_CGS3);
     const Item it = items[blockIdx.x];
-    const BGroup<T> g = groups[it.sys];
+    const BGroup<T, C>& g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
     if (mask) {
-        const SysDesc<T, S, C> sd = sysd[g.sys0];
-        const size_t ld = sd.ldv;
-        const int r0 = it.chunk * sd.rows_per_chunk;
-        const int r1 = min(sd.n, r0 + sd.rows_per_chunk);
         const int na = __popc(mask);
+        const int r0 = it.chunk * g.rpc, r1 = min(g.n, r0 + g.rpc);
         count_work(ctl, K_CGS3, it.chunk,
-                   7.0 * na * sd.n * sizeof(C) + 2.0 * na * sd.n * sizeof(T) + (sd.pinv ? (double)sd.n * sizeof(T) : 0.0),
-                   FmaFlops<C>::v * na * 6.0 * sd.n);
+                   7.0 * na * g.n * sizeof(C) + 2.0 * na * g.n * sizeof(T) + (g.pinv ? (double)g.n * sizeof(T) : 0.0),
+                   FmaFlops<C>::v * na * 6.0 * g.n);
         C alpha[BG_MAXCOL], omega[BG_MAXCOL];
         T* X[BG_MAXCOL];
 #pragma unroll
@@ -580,9 +638,9 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
             omega[q] = on ? cvt<C>(sts[g.sys0 + q].bomega) : zero<C>();
             X[q] = on ? sts[g.sys0 + q].x : nullptr;
         }
-        C* __restrict__ bv = sd.bv;
-        const size_t cs = (size_t)BV_COUNT * ld;
-        const T* __restrict__ pinv = sd.pinv;
+        C* __restrict__ bv = g.bv;
+        const size_t ld = g.ldv, cs = (size_t)BV_COUNT * ld;
+        const T* __restrict__ pinv = g.pinv;
         C acc[2 * BG_MAXCOL];
 #pragma unroll
         for (int q = 0; q < 2 * BG_MAXCOL; ++q) acc[q] = zero<C>();
@@ -651,7 +709,7 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
 __device__ __forceinline__ void bicg_resid_item(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
-                                                const OpDesc* __restrict__ ops, const BGroup<T>& g, int chunk,
+                                                const OpDesc* __restrict__ ops, const BGroup<T, C>& g, int chunk,
                                                 BatchCtl* ctl) {
     const int mask = group_mask(sts, g, PH_RESID);
     if (!mask) return;
@@ -718,7 +776,7 @@ __device__ __forceinline__ void bicg_resid_item(const SysDesc<T, S, C>* __restri
 template <typename T, typename S, typename C>
 __global__ void __launch_bounds__(SYLV_BLOCK)
 k_bicg_resid(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
-             const BGroup<T>* __restrict__ groups, const Item* __restrict__ items, int nitems, BatchCtl* ctl) {
+             const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int nitems, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_RRES);
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {

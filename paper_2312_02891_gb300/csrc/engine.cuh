@@ -95,28 +95,17 @@ int sweep_rows_per_chunk(const std::vector<long long>& sys_rows, int ortho) {
 }
 
 // Rows per work item of the BiCGstab kernels (one item = a row chunk of a
-// group of column systems): one wave of resident blocks of k_bicg_a over the
-// rows of all groups, widened as for the sweeps so that every chunk of the
-// wave has a slot.
+// group of column systems, one block each): at most 768 rows, so that three
+// staged four-column items of a 2D stencil with N <= 256 fit an SM's shared
+// memory, and fewer when the groups' rows would give under eight items per
+// SM (256 at the least).
 template <typename T, typename S, typename C>
 int bicg_rows_per_chunk(const std::vector<long long>& group_rows) {
     long long total_rows = 0;
     for (long long q : group_rows) total_rows += q;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicg_a<T, S, C>, SYLV_BLOCK, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const long long items = (long long)num_sms() * per_sm;
-    long long rpc = (total_rows + items - 1) / items;
-    rpc = std::max<long long>(256, std::min<long long>((rpc + 31) / 32 * 32, 1 << 16));
-    auto chunks = [&](long long c) {
-        long long k = 0;
-        for (long long q : group_rows) k += (q + c - 1) / c;
-        return k;
-    };
-    long long fit = rpc;
-    while (chunks(fit) > items && fit + 32 <= std::min<long long>(rpc + rpc / 4, 1 << 16)) fit += 32;
-    return (int)(chunks(fit) <= items ? fit : rpc);
+    const long long items = (long long)num_sms() * 8;
+    const long long rpc = (total_rows + items - 1) / items;
+    return (int)std::max<long long>(256, std::min<long long>(768, (rpc + 31) / 32 * 32));
 }
 
 // Rows of the BiCGstab groups formed from consecutive column systems with the
@@ -173,15 +162,16 @@ struct Engine {
     int inner = 0;                      // 0: restarted GMRES, 1: BiCGstab
     // BiCGstab: groups of column systems, their work items and vectors
     int ngroups = 0, ngitems = 0;
-    std::vector<BGroup<T>> h_groups;
-    Dev<BGroup<T>> d_groups;
+    std::vector<BGroup<T, C>> h_groups;
+    Dev<BGroup<T, C>> d_groups;
     Dev<Item> d_gitems;
     Dev<C> d_bv;
     Dev<T> d_gpart;
     Dev<unsigned> d_gcount;
-    // dynamic shared memory of k_bicg_a / k_bicg_b: the largest staged work
-    // item (0: every item reads global memory directly)
-    size_t bicg_smem = 0;
+    // BiCGstab step kernels a and b: dynamic shared memory of a staged work
+    // item (the largest one that fits; 0: every item reads global memory
+    // directly)
+    int bicg_smem[2] = {0, 0};
     int restart_every = 1;              // host driver: restart kernels every k-th device iteration
     double kernel_ms[K_COUNT] = {};     // event-timed milliseconds of the sampled launches
     long long samples[K_COUNT] = {};    // sampled launches
@@ -284,36 +274,34 @@ struct Engine {
             h_groups.resize(ngroups);
             gp = 0;
             for (int g = 0; g < ngroups; ++g) {
-                BGroup<T>& bg = h_groups[g];
+                BGroup<T, C>& bg = h_groups[g];
+                const SysDesc<T, S, C>& d0 = h_sd[gs[g].first];
+                const OpDesc& od = ops[d0.op];
+                bg = BGroup<T, C>{};
                 bg.sys0 = gs[g].first;
                 bg.ncol = gs[g].second;
-                bg.nchunks = h_sd[bg.sys0].nchunks;
+                bg.nchunks = d0.nchunks;
                 bg.part = d_gpart.p + gp;
                 bg.counter = d_gcount.p + g;
+                bg.n = d0.n;
+                bg.rpc = d0.rows_per_chunk;
+                bg.ldv = d0.ldv;
+                bg.bv = d0.bv;
+                bg.aval = d0.aval;
+                bg.pinv = d0.pinv;
+                bg.ndiag = od.fmt == 1 ? od.ndiag : 0;
+                for (int d = 0; d < bg.ndiag; ++d) bg.offs[d] = od.offs[d];
+                bg.halo = op_halo_of(bg.offs, bg.ndiag);
+                bg.nnz = (double)od.nnz;
                 gp += (size_t)bg.nchunks * BG_PSTRIDE;
                 for (int c = 0; c < bg.nchunks; ++c) gitems.push_back({g, c});
             }
             ngitems = (int)gitems.size();
             SYLV_TRY(d_groups.alloc(ngroups));
             SYLV_TRY(d_gitems.alloc(gitems.size()));
-            SYLV_CK(cudaMemcpy(d_groups.p, h_groups.data(), ngroups * sizeof(BGroup<T>), cudaMemcpyHostToDevice));
+            SYLV_CK(cudaMemcpy(d_groups.p, h_groups.data(), ngroups * sizeof(BGroup<T, C>), cudaMemcpyHostToDevice));
             SYLV_CK(cudaMemcpy(d_gitems.p, gitems.data(), gitems.size() * sizeof(Item), cudaMemcpyHostToDevice));
-            // staging of the stencil product in shared memory: the largest item
-            // that still leaves room for two blocks per SM
-            bicg_smem = 0;
-            for (const BGroup<T>& bg : h_groups) {
-                const SysDesc<T, S, C>& d0 = h_sd[bg.sys0];
-                if (!d0.aval) continue;
-                const OpDesc& od = ops[d0.op];
-                const size_t b = stage_bytes<C>(rpc, op_halo_of(od.offs, od.ndiag), od.ndiag, bg.ncol, 2, 1);
-                if (b <= SYLV_BICG_SMEM_CAP) bicg_smem = std::max(bicg_smem, b);
-            }
-            if (bicg_smem) {
-                SYLV_CK(cudaFuncSetAttribute(k_bicg_a<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bicg_smem));
-                SYLV_CK(cudaFuncSetAttribute(k_bicg_b<T, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bicg_smem));
-            }
+            SYLV_TRY(bicg_launch_setup());
         }
         SYLV_TRY(d_sd.alloc(nsys));
         SYLV_TRY(d_st.alloc(nsys));
@@ -333,6 +321,25 @@ struct Engine {
         c.nitems = nitems;
         SYLV_CK(cudaMemcpy(d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         for (auto& e : ev) SYLV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return SYLV_OK;
+    }
+
+    // Dynamic shared memory of the staged step kernels a and b: the largest
+    // work item of a stencil group (all columns active) that fits the cap
+    // (larger items read global memory directly).
+    int bicg_launch_setup() {
+        const void* kern[2] = {(const void*)k_bicg_a<T, S, C>, (const void*)k_bicg_b<T, S, C>};
+        for (int k = 0; k < 2; ++k) {
+            size_t cap = 0;
+            for (const auto& bg : h_groups) {
+                if (!bg.aval) continue;
+                const size_t b = k == 0 ? stage_bytes_a<C>(bg.rpc, bg.halo, bg.ndiag, bg.ncol)
+                                        : stage_bytes_b<C>(bg.rpc, bg.halo, bg.ndiag, bg.ncol);
+                if (b <= SYLV_BICG_SMEM_CAP) cap = std::max(cap, b);
+            }
+            bicg_smem[k] = (int)cap;
+            SYLV_CK(cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        }
         return SYLV_OK;
     }
 
@@ -384,11 +391,11 @@ struct Engine {
         };
         if (inner == 1) {
             const dim3 g(ngitems);
-            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, bicg_smem, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
-                            d_ctl.p));
+            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, bicg_smem[0], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+                            bicg_smem[0], d_ctl.p));
             SYLV_TRY(mark(K_SPMV));
-            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, bicg_smem, d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
-                            d_ctl.p));
+            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, bicg_smem[1], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+                            bicg_smem[1], d_ctl.p));
             SYLV_TRY(mark(K_CGS2));
             SYLV_TRY(launch(k_bicg_c<T, S, C>, g, 0, d_sd.p, d_st.p, d_groups.p, d_gitems.p, d_ctl.p));
             SYLV_TRY(mark(K_CGS3));
@@ -1155,14 +1162,14 @@ struct Adi : AdiBase {
         auto* grp = eng.d_groups.p;
         auto* gip = eng.d_gitems.p;
         int ngi = eng.ngitems;
-        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &ctp};
+        int sma = eng.bicg_smem[0], smb = eng.bicg_smem[1];
+        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &sma, &ctp};
+        void* bb[] = {&sdp, &stp, &opp, &grp, &gip, &smb, &ctp};
         void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba,
-                                (int)eng.bicg_smem));
-            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, ba,
-                                (int)eng.bicg_smem));
+            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba, sma));
+            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, bb, smb));
             SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_bicg_c<T, S, C>, ngi, SYLV_BLOCK, bc));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5,
