@@ -277,22 +277,16 @@ KNAMES = {
     "bicgstab": {"arnoldi_spmv": "k_bicg_a (p update + product + rhat^* v)",
                  "cgs_pass2": "k_bicg_b (product + t^* s, t^* t, s^* s)",
                  "cgs_pass3": "k_bicg_c (x, r, q updates + rhat^* r, r^* r)",
-                 "restart_residual": "k_bicg_resid (float64 true residual)"},
+                 "restart_residual": "k_bicg_resid (float64 true residual)",
+                 "restart_update": "k_bicg_list (work list of the iteration)"},
     "dcgs2": {"arnoldi_spmv": "k_dcgs_a (product + all dots)", "cgs_pass3": "k_dcgs_b (basis update)"},
     "cgs2": {},
 }
 INNER_KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
 # DRAM traffic / algorithmic bytes of a kernel from one ncu capture of the
 # current kernels on the same workload, keyed by (inner solver, kernel); a
-# kernel changed after its capture has no entry (traffic null).  BiCGstab:
-# one launch of each step kernel with every column system of the batched
-# workload active (dram__bytes_read.sum + dram__bytes_write.sum over the
-# kernel's own byte model), profiles/bicgstab_batch64_fp32.md.
-NCU_TRAFFIC_RATIO = {
-    ("bicgstab", "arnoldi_spmv"): (172.227072 + 59.132416) / 239.5,    # k_bicg_a
-    ("bicgstab", "cgs_pass2"): (138.055680 + 24.517632) / 171.5,       # k_bicg_b
-    ("bicgstab", "cgs_pass3"): (266.459904 + 97.702144) / 402.2,       # k_bicg_c
-}
+# kernel changed after its capture has no entry (traffic null).
+NCU_TRAFFIC_RATIO = {}
 
 
 def kernel_table(stats, names):

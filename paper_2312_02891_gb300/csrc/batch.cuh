@@ -413,7 +413,22 @@ struct Batch : BatchBase {
     // initial Grams); sweep 1 clears it and a system that finishes sets it,
     // so the outer-step kernels run only in the device iterations after one
     // did (an instance moves on only when all its systems are done).
+    // If the device-updatable step-kernel nodes are refused at
+    // instantiation, the graph is built again without them.
     int build_graph() {
+        int rc = build_graph_once(true);
+        if (rc != SYLV_OK && eng.dyn_grid) {
+            (void)cudaGetLastError();
+            if (gexec) cudaGraphExecDestroy(gexec);
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            gexec = nullptr;
+            rc = build_graph_once(false);
+        }
+        return rc;
+    }
+
+    int build_graph_once(bool try_dyn) {
         cudaGraph_t g;
         SYLV_CK(cudaGraphCreate(&g, 0));
         graph = g;
@@ -462,15 +477,9 @@ struct Batch : BatchBase {
         auto* grp = eng.d_groups.p;
         auto* gip = eng.d_gitems.p;
         int ngi = eng.ngitems;
-        int sma = eng.bicg_smem[0], smb = eng.bicg_smem[1];
-        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &sma, &ctp};
-        void* bb[] = {&sdp, &stp, &opp, &grp, &gip, &smb, &ctp};
-        void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_bicg_a<T, S, C>, ngi, ba, sma));
-            SYLV_TRY(add_kernel(&n2, body, &n1, (void*)k_bicg_b<T, S, C>, ngi, bb, smb));
-            SYLV_TRY(add_kernel(&n3, body, &n2, (void*)k_bicg_c<T, S, C>, ngi, bc));
+            SYLV_TRY(eng.add_bicg_nodes(body, &n_s, &n3, try_dyn));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, body, &n_s, (void*)k_dcgs_a<T, S, C>, ni, a5, dcgs_a_smem_bytes<T, S, C>()));
             SYLV_TRY(add_kernel(&n3, body, &n1, (void*)k_dcgs_b<T, S, C>, ni + nsysb, ab, dcgs_b_smem_bytes<T, S, C>()));
@@ -494,6 +503,8 @@ struct Batch : BatchBase {
             SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, a5));
         }
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
+        // kernels of the graph update nodes of the graph: upload it first
+        if (eng.dyn_grid) SYLV_CK(cudaGraphUpload(gexec, stream));
         BatchCtl c{};
         SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
         c.h_loop = h_loop;
@@ -501,6 +512,7 @@ struct Batch : BatchBase {
         c.h_bouter = h_bouter;
         c.bouter = 1;
         c.nsys = eng.nsys;
+        eng.set_dyn_fields(c);
         SYLV_CK(cudaMemcpy(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         return SYLV_OK;
     }

@@ -331,6 +331,59 @@ __device__ __forceinline__ void bicg_end_cycle(SysState<T>* st) {
 }
 
 // ---------------------------------------------------------------------------
+// Work list of a device iteration: the items (group, chunk) of the groups
+// with an active column, in group order, and its length ctl->nlist (one
+// block).  The step kernels take their items from it; blocks beyond its
+// length return at once.  When a graph drives the solve and its step-kernel
+// nodes are device-updatable, their grids are set to the list's length, so
+// the iterations in which few systems are active launch few blocks.
+// ---------------------------------------------------------------------------
+template <typename T, typename C>
+__global__ void __launch_bounds__(SYLV_BLOCK)
+k_bicg_list(const BGroup<T, C>* __restrict__ groups, int ngroups, const SysState<T>* __restrict__ sts,
+            Item* __restrict__ list, BatchCtl* ctl) {
+    pdl_wait();
+    __shared__ int wsum[SYLV_NWARP];
+    const int per = (ngroups + SYLV_BLOCK - 1) / SYLV_BLOCK;
+    const int g0 = min(ngroups, (int)threadIdx.x * per), g1 = min(ngroups, g0 + per);
+    auto active = [&](int g) {
+        const BGroup<T, C>& gr = groups[g];
+        bool on = false;
+        for (int q = 0; q < gr.ncol; ++q) on |= sts[gr.sys0 + q].phase == PH_ARNOLDI;
+        return on;
+    };
+    int cnt = 0;
+    for (int g = g0; g < g1; ++g)
+        if (active(g)) cnt += groups[g].nchunks;
+    // exclusive prefix sum of cnt over the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = cnt;
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, m);
+        if (lane >= m) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int off = inc - cnt;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    for (int g = g0; g < g1; ++g) {
+        if (!active(g)) continue;
+        const int nc = groups[g].nchunks;
+        for (int c = 0; c < nc; ++c) list[off + c] = Item{g, c};
+        off += nc;
+    }
+    if (threadIdx.x == SYLV_BLOCK - 1) {
+        const int total = off;
+        ctl->nlist = total;
+        if (ctl->graph && ctl->dyn_grid) {
+            const dim3 grid(total > 0 ? total : 1);
+            for (int k = 0; k < 3; ++k) cudaGraphKernelNodeSetGridDim(ctl->dn_step[k], grid);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Step part a: p = r + beta q, v = Op' p, partial rhat^* v.  The last block of
 // a group counts the step and sets alpha = rho / (rhat^* v); a zero or
 // non-finite denominator ends the cycle (breakdown) without an update.
@@ -345,6 +398,7 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         cudaGraphSetConditional(ctl->h_loop, 0u);
         if (ctl->bouter) cudaGraphSetConditional(ctl->h_bouter, 0u);
     }
+    if ((int)blockIdx.x >= ctl->nlist) return;
     const Item it = items[blockIdx.x];
     const BGroup<T, C>& g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
@@ -477,6 +531,7 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
          const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int cap, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_CGS2);
+    if ((int)blockIdx.x >= ctl->nlist) return;
     const Item it = items[blockIdx.x];
     const BGroup<T, C>& g = groups[it.sys];
     const int mask = group_mask(sts, g, PH_ARNOLDI);
@@ -620,9 +675,10 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
          const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_CGS3);
-    const Item it = items[blockIdx.x];
+    const bool inlist = (int)blockIdx.x < ctl->nlist;
+    const Item it = inlist ? items[blockIdx.x] : Item{0, 0};
     const BGroup<T, C>& g = groups[it.sys];
-    const int mask = group_mask(sts, g, PH_ARNOLDI);
+    const int mask = inlist ? group_mask(sts, g, PH_ARNOLDI) : 0;
     if (mask) {
         const int na = __popc(mask);
         const int r0 = it.chunk * g.rpc, r1 = min(g.n, r0 + g.rpc);
@@ -779,10 +835,23 @@ k_bicg_resid(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict_
              const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int nitems, BatchCtl* ctl) {
     pdl_wait();
     count_launch(ctl, K_RRES);
-    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-        const Item it = items[w];
-        bicg_resid_item<T, S, C>(sysd, sts, ops, groups[it.sys], it.chunk, ctl);
-        __syncthreads();          // shared reduction buffers are reused by the next item
+    // this block's items w = blockIdx.x + i * gridDim.x: the threads examine
+    // up to SYLV_BLOCK of them at once, then the block restarts the active ones
+    __shared__ int wl[SYLV_BLOCK];
+    __shared__ int wn;
+    for (int base = blockIdx.x; base < nitems; base += SYLV_BLOCK * gridDim.x) {
+        if (threadIdx.x == 0) wn = 0;
+        __syncthreads();
+        const int w = base + (int)threadIdx.x * (int)gridDim.x;
+        if (w < nitems && group_mask(sts, groups[items[w].sys], PH_RESID)) wl[atomicAdd(&wn, 1)] = w;
+        __syncthreads();
+        const int nw = wn;
+        for (int e = 0; e < nw; ++e) {
+            // any order: each item writes its own partial sums
+            const Item it = items[wl[e]];
+            bicg_resid_item<T, S, C>(sysd, sts, ops, groups[it.sys], it.chunk, ctl);
+            __syncthreads();      // shared reduction buffers are reused by the next item
+        }
     }
     if (ctl->graph) graph_tail<T>(ctl, sts, K_RRES);
 }

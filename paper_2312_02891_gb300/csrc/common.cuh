@@ -397,6 +397,12 @@ struct BatchCtl {
     int bouter;             // 1 when h_bouter belongs to the running graph
     cudaGraphConditionalHandle h_bouter;
     int stage_fault;        // a shared-memory staging wait gave up (the affected columns end non-finite)
+    // BiCGstab work list of the device iteration (items of groups with an
+    // active column) and, in a graph whose step kernels are device-updatable,
+    // their node handles (the list kernel sets their grids to its length)
+    int nlist;
+    int dyn_grid;
+    cudaGraphDeviceNode_t dn_step[3];
 };
 
 __device__ __forceinline__ void count_launch(BatchCtl* ctl, int kid) {

@@ -165,6 +165,7 @@ struct Engine {
     std::vector<BGroup<T, C>> h_groups;
     Dev<BGroup<T, C>> d_groups;
     Dev<Item> d_gitems;
+    Dev<Item> d_glist;                  // work list of the device iteration (k_bicg_list)
     Dev<C> d_bv;
     Dev<T> d_gpart;
     Dev<unsigned> d_gcount;
@@ -299,6 +300,7 @@ struct Engine {
             ngitems = (int)gitems.size();
             SYLV_TRY(d_groups.alloc(ngroups));
             SYLV_TRY(d_gitems.alloc(gitems.size()));
+            SYLV_TRY(d_glist.alloc(gitems.size()));
             SYLV_CK(cudaMemcpy(d_groups.p, h_groups.data(), ngroups * sizeof(BGroup<T, C>), cudaMemcpyHostToDevice));
             SYLV_CK(cudaMemcpy(d_gitems.p, gitems.data(), gitems.size() * sizeof(Item), cudaMemcpyHostToDevice));
             SYLV_TRY(bicg_launch_setup());
@@ -341,6 +343,69 @@ struct Engine {
             SYLV_CK(cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
         }
         return SYLV_OK;
+    }
+
+    // BiCGstab nodes of a graph body: k_bicg_list -> k_bicg_a -> k_bicg_b ->
+    // k_bicg_c after dep (null: none), *last = the node of k_bicg_c.  With
+    // try_dyn the step-kernel nodes are made device-updatable, so that the
+    // list kernel sets their grids to the list's length (dyn_grid = 1 and
+    // their handles in dn on success); otherwise they keep the full grid and
+    // their blocks beyond the list return at once.
+    int dyn_grid = 0;
+    cudaGraphDeviceNode_t dn[3] = {};
+    int add_bicg_nodes(cudaGraph_t body, cudaGraphNode_t* dep, cudaGraphNode_t* last, bool try_dyn) {
+        auto add = [&](cudaGraphNode_t* node, cudaGraphNode_t* d, void* func, int grid, void** args, int smem) {
+            cudaKernelNodeParams kp = {};
+            kp.func = func;
+            kp.gridDim = dim3(grid);
+            kp.blockDim = dim3(SYLV_BLOCK);
+            kp.sharedMemBytes = smem;
+            kp.kernelParams = args;
+            kp.extra = nullptr;
+            return cudaGraphAddKernelNode(node, body, d, d ? 1 : 0, &kp);
+        };
+        auto* sdp = d_sd.p;
+        auto* stp = d_st.p;
+        auto* opp = d_ops.p;
+        auto* grp = d_groups.p;
+        auto* glp = d_glist.p;
+        auto* ctp = d_ctl.p;
+        int ng = ngroups, sma = bicg_smem[0], smb = bicg_smem[1];
+        void* al[] = {&grp, &ng, &stp, &glp, &ctp};
+        void* aa[] = {&sdp, &stp, &opp, &grp, &glp, &sma, &ctp};
+        void* ab[] = {&sdp, &stp, &opp, &grp, &glp, &smb, &ctp};
+        void* ac[] = {&sdp, &stp, &grp, &glp, &ctp};
+        cudaGraphNode_t nl, n[3];
+        SYLV_CK(add(&nl, dep, (void*)k_bicg_list<T, C>, 1, al, 0));
+        SYLV_CK(add(&n[0], &nl, (void*)k_bicg_a<T, S, C>, ngitems, aa, sma));
+        SYLV_CK(add(&n[1], &n[0], (void*)k_bicg_b<T, S, C>, ngitems, ab, smb));
+        SYLV_CK(add(&n[2], &n[1], (void*)k_bicg_c<T, S, C>, ngitems, ac, 0));
+        *last = n[2];
+        dyn_grid = 0;
+        if (!try_dyn) return SYLV_OK;
+        for (int k = 0; k < 3; ++k) {
+            cudaKernelNodeAttrValue v = {};
+            v.deviceUpdatableKernelNode.deviceUpdatable = 1;
+            cudaKernelNodeAttrValue o = {};
+            if (cudaGraphKernelNodeSetAttribute(n[k], cudaKernelNodeAttributeDeviceUpdatableKernelNode, &v) !=
+                    cudaSuccess ||
+                cudaGraphKernelNodeGetAttribute(n[k], cudaKernelNodeAttributeDeviceUpdatableKernelNode, &o) !=
+                    cudaSuccess ||
+                !o.deviceUpdatableKernelNode.devNode) {
+                (void)cudaGetLastError();
+                return SYLV_OK;
+            }
+            dn[k] = o.deviceUpdatableKernelNode.devNode;
+        }
+        dyn_grid = 1;
+        return SYLV_OK;
+    }
+
+    // The control block's work-list fields of a graph built with
+    // add_bicg_nodes (device handles, whether the grids follow the list).
+    void set_dyn_fields(BatchCtl& c) const {
+        c.dyn_grid = dyn_grid;
+        for (int k = 0; k < 3; ++k) c.dn_step[k] = dyn_grid ? dn[k] : cudaGraphDeviceNode_t{};
     }
 
     // Blocks of the restart kernels (grid-stride over the work items).
@@ -391,13 +456,15 @@ struct Engine {
         };
         if (inner == 1) {
             const dim3 g(ngitems);
-            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, bicg_smem[0], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+            SYLV_TRY(launch(k_bicg_list<T, C>, dim3(1), 0, d_groups.p, ngroups, d_st.p, d_glist.p, d_ctl.p));
+            SYLV_TRY(mark(K_RUPD));
+            SYLV_TRY(launch(k_bicg_a<T, S, C>, g, bicg_smem[0], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_glist.p,
                             bicg_smem[0], d_ctl.p));
             SYLV_TRY(mark(K_SPMV));
-            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, bicg_smem[1], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_gitems.p,
+            SYLV_TRY(launch(k_bicg_b<T, S, C>, g, bicg_smem[1], d_sd.p, d_st.p, d_ops.p, d_groups.p, d_glist.p,
                             bicg_smem[1], d_ctl.p));
             SYLV_TRY(mark(K_CGS2));
-            SYLV_TRY(launch(k_bicg_c<T, S, C>, g, 0, d_sd.p, d_st.p, d_groups.p, d_gitems.p, d_ctl.p));
+            SYLV_TRY(launch(k_bicg_c<T, S, C>, g, 0, d_sd.p, d_st.p, d_groups.p, d_glist.p, d_ctl.p));
             SYLV_TRY(mark(K_CGS3));
             if (with_restart) {
                 SYLV_TRY(launch(k_bicg_resid<T, S, C>, dim3(restart_grid()), 0, d_sd.p, d_st.p, d_ops.p, d_groups.p,
@@ -1122,7 +1189,22 @@ struct Adi : AdiBase {
         return SYLV_OK;
     }
 
+    // The graph of a solve; if the device-updatable step-kernel nodes are
+    // refused at instantiation, the graph is built again without them.
     int build_graph() {
+        int rc = build_graph_once(true);
+        if (rc != SYLV_OK && eng.dyn_grid) {
+            (void)cudaGetLastError();
+            if (gexec) cudaGraphExecDestroy(gexec);
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            gexec = nullptr;
+            rc = build_graph_once(false);
+        }
+        return rc;
+    }
+
+    int build_graph_once(bool try_dyn) {
         const int nb = d.nchA + d.nchB;
         const int ni = eng.nitems;
         int one = 1, zero = 0, mode0 = 0;
@@ -1162,15 +1244,9 @@ struct Adi : AdiBase {
         auto* grp = eng.d_groups.p;
         auto* gip = eng.d_gitems.p;
         int ngi = eng.ngitems;
-        int sma = eng.bicg_smem[0], smb = eng.bicg_smem[1];
-        void* ba[] = {&sdp, &stp, &opp, &grp, &gip, &sma, &ctp};
-        void* bb[] = {&sdp, &stp, &opp, &grp, &gip, &smb, &ctp};
-        void* bc[] = {&sdp, &stp, &grp, &gip, &ctp};
         void* br[] = {&sdp, &stp, &opp, &grp, &gip, &ngi, &ctp};
         if (eng.inner == 1) {
-            SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_bicg_a<T, S, C>, ngi, SYLV_BLOCK, ba, sma));
-            SYLV_TRY(add_kernel(&n2, loop_body, &n1, (void*)k_bicg_b<T, S, C>, ngi, SYLV_BLOCK, bb, smb));
-            SYLV_TRY(add_kernel(&n3, loop_body, &n2, (void*)k_bicg_c<T, S, C>, ngi, SYLV_BLOCK, bc));
+            SYLV_TRY(eng.add_bicg_nodes(loop_body, nullptr, &n3, try_dyn));
         } else if (eng.ortho == 1) {
             SYLV_TRY(add_kernel(&n1, loop_body, nullptr, (void*)k_dcgs_a<T, S, C>, ni, SYLV_BLOCK, a5,
                                 dcgs_a_smem_bytes<T, S, C>()));
@@ -1190,6 +1266,8 @@ struct Adi : AdiBase {
             SYLV_TRY(add_kernel(&n5, if_body, &n4, (void*)k_restart_residual<T, S, C>, rg, SYLV_BLOCK, a5));
         }
         SYLV_CK(cudaGraphInstantiate(&gexec, g, 0));
+        // kernels of the graph update nodes of the graph: upload it first
+        if (eng.dyn_grid) SYLV_CK(cudaGraphUpload(gexec, stream));
         // the kernels read the handles and the decision parameters from the control block
         BatchCtl c{};
         SYLV_CK(cudaMemcpy(&c, eng.d_ctl.p, sizeof(c), cudaMemcpyDeviceToHost));
@@ -1199,6 +1277,7 @@ struct Adi : AdiBase {
         c.nsys = eng.nsys;
         c.max_ticks = max_inner + 8;
         c.graph = 0;
+        eng.set_dyn_fields(c);
         SYLV_CK(cudaMemcpy(eng.d_ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
         return SYLV_OK;
     }

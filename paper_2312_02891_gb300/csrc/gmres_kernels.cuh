@@ -607,7 +607,11 @@ __device__ void graph_tail(BatchCtl* ctl, SysState<T>* sts, int kid) {
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = ((atomicAdd(&ctl->gdone[kid], 1u) + 1u) % gridDim.x) == 0u;
+    if (threadIdx.x == 0) {
+        s_last = atomicAdd(&ctl->gdone[kid], 1u) + 1u == gridDim.x;
+        // the last block resets the count: the next launch may have another grid
+        if (s_last) ctl->gdone[kid] = 0u;
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
