@@ -285,8 +285,15 @@ KNAMES = {
 INNER_KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
 # DRAM traffic / algorithmic bytes of a kernel from one ncu capture of the
 # current kernels on the same workload, keyed by (inner solver, kernel); a
-# kernel changed after its capture has no entry (traffic null).
-NCU_TRAFFIC_RATIO = {}
+# kernel changed after its capture has no entry (traffic null).  BiCGstab:
+# one launch of each step kernel with every column system of the batched
+# workload active (dram__bytes_read.sum + dram__bytes_write.sum over the
+# kernel's own byte model), profiles/bicgstab_batch64_fp32.md.
+NCU_TRAFFIC_RATIO = {
+    ("bicgstab", "arnoldi_spmv"): (172.304640 + 45.247232) / 239.5,    # k_bicg_a
+    ("bicgstab", "cgs_pass2"): (138.174464 + 19.597824) / 171.5,       # k_bicg_b
+    ("bicgstab", "cgs_pass3"): (266.494464 + 93.886464) / 402.2,       # k_bicg_c
+}
 
 
 def kernel_table(stats, names):

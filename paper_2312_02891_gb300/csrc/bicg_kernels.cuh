@@ -662,6 +662,66 @@ k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
     if (threadIdx.x == 0) *g.counter = 0;
 }
 
+// Kernel c with float32 vectors: four consecutive rows per thread, 16-byte
+// loads and stores of the vectors (their columns start on 32-row
+// boundaries, so a row index that is a multiple of four is 16-byte aligned);
+// the rows of a ragged end are stored one by one (rows in [n, ldv) stay
+// zero).  Same arithmetic per row as the generic loop.
+template <typename T>
+__device__ __forceinline__ void bicg_c_rows4(float* __restrict__ bv, size_t ld, const T* __restrict__ pinv, int mask,
+                                             const float (&alpha)[BG_MAXCOL], const float (&omega)[BG_MAXCOL],
+                                             T* const (&X)[BG_MAXCOL], int r0, int r1, float (&acc)[2 * BG_MAXCOL]) {
+    const size_t cs = (size_t)BV_COUNT * ld;
+    const int m = r1 - r0;
+    auto ld4 = [](const float* a) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(a));
+        return v;
+    };
+    for (int e0 = 4 * (int)threadIdx.x; e0 < m; e0 += 4 * (int)blockDim.x) {
+        const int i = r0 + e0;
+        const int ne = min(4, m - e0);
+        T pi[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pi[e] = (pinv && e < ne) ? ldro(pinv + i + e) : make_scalar<T>(1.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < BG_MAXCOL; ++q) {
+            if (!(mask >> q & 1)) continue;
+            float* c = bv + q * cs + (size_t)i;
+            const float4 p4 = ld4(c + BV_P * ld), v4 = ld4(c + BV_V * ld), r4 = ld4(c + BV_R * ld);
+            const float4 t4 = ld4(c + BV_T * ld), h4 = ld4(c + BV_RH * ld);
+            T xo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) xo[e] = e < ne ? ldro(X[q] + i + e) : zero<T>();
+            const float pa[4] = {p4.x, p4.y, p4.z, p4.w}, va[4] = {v4.x, v4.y, v4.z, v4.w};
+            const float ra[4] = {r4.x, r4.y, r4.z, r4.w}, ta[4] = {t4.x, t4.y, t4.z, t4.w};
+            const float ha[4] = {h4.x, h4.y, h4.z, h4.w};
+            float rn[4], qn[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float sv = ra[e] - alpha[q] * va[e];
+                if (e < ne) X[q][i + e] = xo[e] + pi[e] * cvt<T>(alpha[q] * pa[e] + omega[q] * sv);
+                rn[e] = sv - omega[q] * ta[e];
+                qn[e] = pa[e] - omega[q] * va[e];
+                if (e < ne) {
+                    acc[2 * q] += ha[e] * rn[e];
+                    acc[2 * q + 1] += rn[e] * rn[e];
+                }
+            }
+            if (ne == 4) {
+                *reinterpret_cast<float4*>(c + BV_R * ld) = make_float4(rn[0], rn[1], rn[2], rn[3]);
+                *reinterpret_cast<float4*>(c + BV_Q * ld) = make_float4(qn[0], qn[1], qn[2], qn[3]);
+            } else {
+                for (int e = 0; e < ne; ++e) {
+                    c[BV_R * ld + e] = rn[e];
+                    c[BV_Q * ld + e] = qn[e];
+                }
+            }
+        }
+    }
+}
+template <typename T, typename C> struct BicgRows4 { static constexpr bool value = false; };
+template <typename T> struct BicgRows4<T, float> { static constexpr bool value = true; };
+
 // ---------------------------------------------------------------------------
 // Step part c: x += P^{-1}(alpha p + omega s) in float64, r = s - omega t,
 // q = p - omega v, partial rhat^* r and r^* r.  The last block records the
@@ -702,23 +762,27 @@ k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
         for (int q = 0; q < 2 * BG_MAXCOL; ++q) acc[q] = zero<C>();
         // every element is read and then overwritten by the same thread only:
         // read-only loads, so the next row's loads may pass this row's stores
+        if constexpr (BicgRows4<T, C>::value) {
+            bicg_c_rows4<T>(bv, ld, pinv, mask, alpha, omega, X, r0, r1, acc);
+        } else {
 #pragma unroll 2
-        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const T pi = pinv ? ldro(pinv + i) : make_scalar<T>(1.0, 0.0);
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                const T pi = pinv ? ldro(pinv + i) : make_scalar<T>(1.0, 0.0);
 #pragma unroll
-            for (int q = 0; q < BG_MAXCOL; ++q) {
-                if (mask >> q & 1) {
-                    C* c = bv + q * cs + (size_t)i;
-                    const C p = ldro(c + BV_P * ld), v = ldro(c + BV_V * ld), r = ldro(c + BV_R * ld);
-                    const C t = ldro(c + BV_T * ld), rh = ldro(c + BV_RH * ld);
-                    const T xo = ldro(X[q] + i);
-                    const C s = r - alpha[q] * v;
-                    X[q][i] = xo + pi * cvt<T>(alpha[q] * p + omega[q] * s);
-                    const C rn = s - omega[q] * t;
-                    c[BV_R * ld] = rn;
-                    c[BV_Q * ld] = p - omega[q] * v;
-                    acc[2 * q] += cmul(rh, rn);
-                    acc[2 * q + 1] += from_real<C>(abs2(rn));
+                for (int q = 0; q < BG_MAXCOL; ++q) {
+                    if (mask >> q & 1) {
+                        C* c = bv + q * cs + (size_t)i;
+                        const C p = ldro(c + BV_P * ld), v = ldro(c + BV_V * ld), r = ldro(c + BV_R * ld);
+                        const C t = ldro(c + BV_T * ld), rh = ldro(c + BV_RH * ld);
+                        const T xo = ldro(X[q] + i);
+                        const C s = r - alpha[q] * v;
+                        X[q][i] = xo + pi * cvt<T>(alpha[q] * p + omega[q] * s);
+                        const C rn = s - omega[q] * t;
+                        c[BV_R * ld] = rn;
+                        c[BV_Q * ld] = p - omega[q] * v;
+                        acc[2 * q] += cmul(rh, rn);
+                        acc[2 * q + 1] += from_real<C>(abs2(rn));
+                    }
                 }
             }
         }
