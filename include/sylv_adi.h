@@ -36,7 +36,7 @@ extern "C" {
 /* ---- status codes ---- */
 #define SYLV_OK                 0
 #define SYLV_ERR_INVALID       -1   /* bad argument (null pointer, size, CSR structure) */
-#define SYLV_ERR_CUDA          -2   /* a CUDA runtime call failed */
+#define SYLV_ERR_CUDA          -2   /* a CUDA runtime call failed, or a bounded wait in a kernel gave up */
 #define SYLV_ERR_NOMEM         -3   /* device or host allocation failed */
 #define SYLV_ERR_MAXIT         -4   /* kmax outer steps without reaching tau; factors valid */
 #define SYLV_ERR_INNER_STALL   -5   /* an inner solve hit max_inner before its tolerance */

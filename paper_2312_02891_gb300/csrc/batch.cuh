@@ -549,6 +549,7 @@ struct Batch : BatchBase {
 
     // Per-instance status of the finished solve (SYLV_OK or the first failure).
     int finish() {
+        SYLV_TRY(eng.take_stage_fault());
         std::vector<AdiState<T>> hs(count);
         SYLV_CK(cudaMemcpy(hs.data(), st.p, (size_t)count * sizeof(AdiState<T>), cudaMemcpyDeviceToHost));
         solved = 1;

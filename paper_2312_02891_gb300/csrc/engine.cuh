@@ -408,6 +408,19 @@ struct Engine {
         for (int k = 0; k < 3; ++k) c.dn_step[k] = dyn_grid ? dn[k] : cudaGraphDeviceNode_t{};
     }
 
+    // Reports (and clears) a shared-memory staging wait of the BiCGstab
+    // kernels that gave up during the last solve; the columns it touched
+    // then hold non-finite values.
+    int take_stage_fault() {
+        int f = 0;
+        SYLV_CK(cudaMemcpy(&f, &d_ctl.p->stage_fault, sizeof(int), cudaMemcpyDeviceToHost));
+        if (!f) return SYLV_OK;
+        const int z = 0;
+        SYLV_CK(cudaMemcpy(&d_ctl.p->stage_fault, &z, sizeof(int), cudaMemcpyHostToDevice));
+        set_error("a shared-memory staging wait of the BiCGstab kernels gave up; the affected columns are not finite");
+        return SYLV_ERR_CUDA;
+    }
+
     // Blocks of the restart kernels (grid-stride over the work items).
     int restart_grid() const { return std::max(1, std::min(inner == 1 ? ngitems : nitems, 2 * num_sms())); }
 
@@ -828,6 +841,7 @@ int krylov_t(const DevOp& op, T sigma, int jacobi, const void* B, void* X, int n
     *eng.h_flag = 1;
     SYLV_TRY(eng.run((long long)max_iters + 8));
     SYLV_CK(cudaStreamSynchronize(s));
+    SYLV_TRY(eng.take_stage_fault());
     SYLV_CK(cudaMemcpy(st.data(), eng.d_st.p, ncols * sizeof(SysState<T>), cudaMemcpyDeviceToHost));
     int stalled = 0;
     for (int c = 0; c < ncols; ++c) {
@@ -1292,6 +1306,7 @@ struct Adi : AdiBase {
 
     int finish_solve(unsigned long long l0) {
         SYLV_CK(cudaStreamSynchronize(stream));
+        SYLV_TRY(eng.take_stage_fault());
         launches_last = (long long)(device_launches() - l0);
         AdiState<T> s;
         SYLV_CK(cudaMemcpy(&s, st.p, sizeof(s), cudaMemcpyDeviceToHost));

@@ -7,6 +7,8 @@ writes tests/golden/<workload>_<strategy>.json with the outer step count,
 the per-step controller history, inner iteration totals, the computed and
 true relative residuals, and a two-sided sketch S = P^T X Q of the factored
 solution (P: n x 16, Q: m x 16 seeded Gaussian, streams 5 and 6).
+``python tests/golden/make_golden.py real mid3d nobl_mid bicgstab`` writes the
+real double step for complex shift pairs on a named workload, with its shifts.
 ``python tests/golden/make_golden.py batch64 nobl_mid bicgstab`` writes the
 same per instance of the 64-instance batched workload (8 x 8 sketches, and the
 shifts each instance was solved with).
@@ -111,7 +113,39 @@ def main_batch(strategy: str, inner: str, count: int = 64, workers: int = 8):
     print(path, sum(r["steps"] for r in rows), f"{time.time() - t0:.0f}s")
 
 
+def main_real(workload: str, strategy: str, inner: str):
+    """tests/golden/<workload>_<strategy>_<inner>_real.json: the real double
+    step for complex shift pairs (oracle/lradi_real.py) on a named workload:
+    outer steps, computed residual, inner totals, a 16 x 16 sketch of
+    X = Z Gamma Y^T and the shifts it was solved with (the generator's
+    choice can differ with the host's BLAS/LAPACK)."""
+    from oracle.lradi_real import lradi_real
+    p = W.problem_config(workload)
+    t0 = time.time()
+    res = lradi_real(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, strategy=strategy,
+                     jacobi=p.opts.get("jacobi", False), restart=p.opts.get("restart", 30), inner=inner)
+    wall = time.time() - t0
+    P, Q = sketch_mats(p.A.n, p.B.n)
+    S = (P.T @ res.Z) @ res.Gamma @ (res.Y.T @ Q)
+    hist = [{k: (float(np.real(v)) if not isinstance(v, (bool, np.bool_)) else bool(v))
+             for k, v in h.items() if np.isscalar(v)} for h in res.history]
+    out = dict(workload=workload, strategy=strategy, inner=inner, real_pairs=True, tau=p.tau,
+               n=p.A.n, m=p.B.n, r=p.r, steps=res.steps, converged=bool(res.converged), res_comp=res.res_comp,
+               inner_its_A=res.inner_its_A, inner_its_B=res.inner_its_B, complex_solves=res.complex_solves,
+               alpha=[[float(np.real(a)), float(np.imag(a))] for a in p.alpha],
+               beta=[[float(np.real(b)), float(np.imag(b))] for b in p.beta],
+               sketch=np.real(S).tolist(), sketch_fro=float(np.linalg.norm(S)), oracle_wall_s=wall, history=hist)
+    path = os.path.join(HERE, f"{workload}_{strategy}_{inner}_real.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(path, res.steps, res.res_comp, res.inner_its_A, res.inner_its_B, f"{wall:.0f}s")
+
+
 if __name__ == "__main__":
+    if len(sys.argv) > 1 and sys.argv[1] == "real":
+        main_real(sys.argv[2], sys.argv[3] if len(sys.argv) > 3 else "nobl_mid",
+                  sys.argv[4] if len(sys.argv) > 4 else "bicgstab")
+        sys.exit(0)
     if len(sys.argv) > 1 and sys.argv[1] == "batch64":
         main_batch(sys.argv[2] if len(sys.argv) > 2 else "nobl_mid", sys.argv[3] if len(sys.argv) > 3 else "bicgstab")
         sys.exit(0)
