@@ -594,7 +594,7 @@ struct Engine {
 // vectors with a fixed pseudo-random pattern and the operators' stencil
 // values with a diagonally dominant stencil of the same diagonals (so the
 // iteration neither breaks down nor converges during the probe), and times
-// device iterations with CUDA events: BiCGstab 2 + 6 steps, GMRES one cycle.
+// device iterations with CUDA events: BiCGstab 2 + 12 steps, GMRES one cycle.
 // The fastest candidate wins; every candidate and its time are kept.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_pattern(double& x, double u, double) { x = u; }
@@ -659,8 +659,13 @@ int autotune_rpc(const std::vector<int>& sys_n, const std::vector<int>& sys_op, 
         k_fill_stencil<C><<<num_sms() * 2, 256, 0, s>>>(tav[q].p, od);
         av[q] = tav[q].p;
     }
+    // one solution vector per system (a shared one would make the update
+    // kernel's stores of all systems collide on the same addresses)
     Dev<T> xs;
-    SYLV_TRY(xs.alloc((size_t)nmax));
+    size_t xtot = 0;
+    for (int q : sys_n) xtot += (size_t)q;
+    SYLV_TRY(xs.alloc(xtot));
+    SYLV_CK(cudaMemsetAsync(xs.p, 0, xtot * sizeof(T), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SYLV_CK(cudaEventCreate(&e0));
     SYLV_CK(cudaEventCreate(&e1));
@@ -682,12 +687,14 @@ int autotune_rpc(const std::vector<int>& sys_n, const std::vector<int>& sys_op, 
             k_fill_pattern<S><<<num_sms() * 4, 256, 0, s>>>(eng.d_V.p, eng.d_V.count, 12345u);
         }
         std::vector<SysState<T>> st(nsys);
+        size_t xo = 0;
         for (int q = 0; q < nsys; ++q) {
             std::memset(&st[q], 0, sizeof(SysState<T>));
             st[q].phase = PH_ARNOLDI;
             st[q].max_iters = 1 << 30;
             st[q].tol = 0.0;
-            st[q].x = xs.p;
+            st[q].x = xs.p + xo;
+            xo += (size_t)sys_n[q];
             st[q].scale[0] = 1.0;
             st[q].g[0] = make_scalar<T>(1.0, 0.0);
             st[q].brho = make_scalar<T>(1.0, 0.0);
@@ -701,7 +708,7 @@ int autotune_rpc(const std::vector<int>& sys_n, const std::vector<int>& sys_op, 
         cc.n_active = nsys;
         cc.nitems = eng.nitems;
         SYLV_CK(cudaMemcpyAsync(eng.d_ctl.p, &cc, sizeof(cc), cudaMemcpyHostToDevice, s));
-        const int warm = inner == 1 ? 2 : 0, timed = inner == 1 ? 6 : std::max(1, restart - 1);
+        const int warm = inner == 1 ? 2 : 0, timed = inner == 1 ? 12 : std::max(1, restart - 1);
         for (int t = 0; t < warm; ++t) SYLV_TRY(eng.launch_tick(0, 0, false));
         SYLV_CK(cudaEventRecord(e0, s));
         for (int t = 0; t < timed; ++t) SYLV_TRY(eng.launch_tick(0, 0, false));
