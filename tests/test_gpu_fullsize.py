@@ -120,6 +120,34 @@ def test_mid3d_complex_mixed_precision_sampled_residual():
     assert np.abs(X.imag).max() <= 1e-5 * np.abs(X.real).max()
 
 
+def test_mid3d_real_pairs_matches_stored_oracle_run():
+    """Configuration 3 at full size (A: 3D N = 128, n = 2,097,152; B: N = 100,
+    m = 1,000,000; r = 4; 16 complex shift pairs) with the real double step
+    and float32 BiCGstab, against the stored float64 oracle run of the same
+    method (tests/golden/mid3d_nobl_mid_bicgstab_real.json, written by
+    make_golden.py with oracle/lradi_real.py), solved with its shifts: outer
+    steps within +-1, the computed residual below tau, and the 16 x 16 sketch
+    P^T X Q of X = Z G Y^T within 1e-3 of the oracle's (two valid BiCGstab runs
+    differ by solution errors of order tau times the conditioning, as for the
+    batched workload)."""
+    g = golden("mid3d_nobl_mid_bicgstab_real")
+    p = W.problem_config("mid3d")
+    p = dataclasses.replace(p, alpha=stored_shifts(g["alpha"]), beta=stored_shifts(g["beta"]))
+    with P.SylvesterADI(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, jacobi=1, strategy="nobl_mid",
+                        precision="fp32", inner="bicgstab", real_pairs=1) as s:
+        assert s.solve() == 0, P.sylv_last_error()
+        info = s.info()
+        Z, Y, G = s.factors()
+    assert abs(info["steps"] - g["steps"]) <= 1, (info["steps"], g["steps"])
+    assert info["rel_res_comp"] < p.tau
+    Pm, Qm = _golden_module().sketch_mats(p.A.n, p.B.n)
+    S = (Pm.T @ Z) @ G @ (Y.T @ Qm)
+    S0 = np.asarray(g["sketch"])
+    rel = np.linalg.norm(S - S0) / np.linalg.norm(S0)
+    assert rel <= 1e-3, rel
+    print("mid3d real pairs: steps %d (oracle %d), sketch difference %.2e" % (info["steps"], g["steps"], rel))
+
+
 def test_mid2d_literal_back_looking_stagnates_like_the_oracle(mid):
     """With eq. (ADI_relax2_prak) taken literally the tolerances outgrow ||w||
     on this workload and the iteration stalls near 3e-7 at kmax = 50; the GPU
