@@ -284,15 +284,16 @@ KNAMES = {
 }
 INNER_KERNELS = ("arnoldi_spmv", "cgs_pass2", "cgs_pass3")
 # DRAM traffic / algorithmic bytes of a kernel from one ncu capture of the
-# current kernels on the same workload, keyed by (inner solver, kernel); a
-# kernel changed after its capture has no entry (traffic null).  BiCGstab:
+# current kernels, keyed by (workload, precision, inner solver, kernel); a
+# kernel changed after its capture, or another workload or precision, has no
+# entry (traffic null).  BiCGstab:
 # one launch of each step kernel with every column system of the batched
 # workload active (dram__bytes_read.sum + dram__bytes_write.sum over the
 # kernel's own byte model), profiles/bicgstab_batch64_fp32.md.
 NCU_TRAFFIC_RATIO = {
-    ("bicgstab", "arnoldi_spmv"): (172.304640 + 45.247232) / 239.5,    # k_bicg_a
-    ("bicgstab", "cgs_pass2"): (138.174464 + 19.597824) / 171.5,       # k_bicg_b
-    ("bicgstab", "cgs_pass3"): (266.494464 + 93.886464) / 402.2,       # k_bicg_c
+    ("batch64", "fp32", "bicgstab", "arnoldi_spmv"): (172.304640 + 45.247232) / 239.5,    # k_bicg_a
+    ("batch64", "fp32", "bicgstab", "cgs_pass2"): (138.174464 + 19.597824) / 171.5,       # k_bicg_b
+    ("batch64", "fp32", "bicgstab", "cgs_pass3"): (266.494464 + 93.886464) / 402.2,       # k_bicg_c
 }
 
 
@@ -305,11 +306,11 @@ def kernel_table(stats, names):
             for k, v in stats.items() if v[3] > 0}
 
 
-def roofline_of(stats, names, hbm, hbm_src, inner):
+def roofline_of(stats, names, hbm, hbm_src, inner, workload, precision):
     dom = max(INNER_KERNELS, key=lambda k: stats[k][0])
     ms, by, fl, la = stats[dom]
     ach = (by / la) / ((ms / la) * 1e-3) / 1e9 if ms > 0 else None
-    ratio = NCU_TRAFFIC_RATIO.get((inner, dom))
+    ratio = NCU_TRAFFIC_RATIO.get((workload, precision, inner, dom))
     inner_ms = sum(stats[k][0] for k in INNER_KERNELS + ("restart_update", "restart_residual"))
     inner_by = sum(stats[k][1] for k in INNER_KERNELS + ("restart_update", "restart_residual"))
     return {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": ach, "peak": hbm, "unit": "GB/s",
@@ -448,7 +449,7 @@ def run_ours(a):
     stats = prof.kernel_stats()
     prof.profile(False)
     prof.close()
-    roof = roofline_of(stats, names, hbm, hbm_src, a.inner)
+    roof = roofline_of(stats, names, hbm, hbm_src, a.inner, a.workload, a.precision)
 
     # ---------------- end to end through the public API, host buffers ----------------
     e2e_steps = max(1, min(a.steps, 3))
