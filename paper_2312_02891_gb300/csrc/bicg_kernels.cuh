@@ -30,6 +30,17 @@ namespace sylv {
 constexpr int BG_MAXCOL = 4;                     // columns of a group (the rank cap)
 constexpr int BG_PSTRIDE = 3 * BG_MAXCOL;        // partial sums per chunk (at most 3 per column)
 
+// Resident blocks per SM the step kernels are compiled for (their register
+// budget): the staged stencil kernels a and b hold three blocks per SM in
+// shared memory anyway; the streaming update kernel c keeps more blocks for
+// loads in flight.  complex128 needs twice the registers per value: two
+// blocks per SM keep its kernels free of large spills.
+template <typename C> struct BicgOccAB { static constexpr int value = 3; };
+template <> struct BicgOccAB<cplx> { static constexpr int value = 2; };
+template <typename C> struct BicgOccC { static constexpr int value = 3; };
+template <> struct BicgOccC<float> { static constexpr int value = 4; };
+template <> struct BicgOccC<cplx> { static constexpr int value = 2; };
+
 // Vectors of one BiCGstab system, column-major, ldv apart, C precision.
 enum BVec : int { BV_R = 0, BV_Q = 1, BV_P = 2, BV_V = 3, BV_T = 4, BV_RH = 5, BV_COUNT = 6 };
 
@@ -389,7 +400,7 @@ k_bicg_list(const BGroup<T, C>* __restrict__ groups, int ngroups, const SysState
 // non-finite denominator ends the cycle (breakdown) without an update.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, 3)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOccAB<C>::value)
 k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
          const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int cap, BatchCtl* ctl) {
     pdl_wait();
@@ -526,7 +537,7 @@ k_bicg_a(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ st
 // when ||s|| already meets the tolerance.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, 3)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOccAB<C>::value)
 k_bicg_b(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts, const OpDesc* __restrict__ ops,
          const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, int cap, BatchCtl* ctl) {
     pdl_wait();
@@ -730,7 +741,7 @@ template <typename T> struct BicgRows4<T, float> { static constexpr bool value =
 // beta' = (rho' / rho)(alpha / omega).
 // ---------------------------------------------------------------------------
 template <typename T, typename S, typename C>
-__global__ void __launch_bounds__(SYLV_BLOCK, 4)
+__global__ void __launch_bounds__(SYLV_BLOCK, BicgOccC<C>::value)
 k_bicg_c(const SysDesc<T, S, C>* __restrict__ sysd, SysState<T>* __restrict__ sts,
          const BGroup<T, C>* __restrict__ groups, const Item* __restrict__ items, BatchCtl* ctl) {
     pdl_wait();
