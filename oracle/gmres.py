@@ -282,7 +282,7 @@ def _gmres_dcgs2(S, sigma, b, tol, m, max_iters, pinv, dtype, mass=None, x0=None
 
 
 def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = False,
-             mass=None, x0=None) -> GmresResult:
+             mass=None, x0=None, trace=None) -> GmresResult:
     """BiCGstab (van der Vorst, SIAM J. Sci. Stat. Comput. 13 (1992)) for
     (S + sigma I) x = b, or (S + sigma Mass) x = b, with right Jacobi
     preconditioning: the short-recurrence inner solver the paper uses for
@@ -292,7 +292,9 @@ def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = Fal
     if it is not below tol, the method starts again from the current iterate
     (fresh shadow vector).  iters counts BiCGstab steps (two operator
     applications each); history holds the recurrence residual norms.  A
-    breakdown (rho or the step denominator zero) restarts the same way."""
+    breakdown (rho or the step denominator zero) restarts the same way.
+    trace (tests only): called after every full step with the step's vectors
+    rhat, v, s, t and the new residual r."""
     dtype = np.result_type(S.dtype, np.asarray(sigma).dtype, b.dtype)
     n = b.shape[0]
     b = b.astype(dtype)
@@ -333,6 +335,8 @@ def bicgstab(S, sigma, b, tol: float, max_iters: int = 20000, jacobi: bool = Fal
             omega = np.vdot(t, s) / tt if tt > 0.0 else 0.0
             x = x + alpha * ph + omega * sh
             r = s - omega * t
+            if trace is not None:
+                trace(dict(rhat=rhat, v=v, s=s, t=t, r=r))
             rho = rho_new
             hist.append(np.linalg.norm(r))
             if hist[-1] <= tol:

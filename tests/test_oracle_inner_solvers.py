@@ -57,6 +57,25 @@ def test_bicgstab_matches_sparse_solve(tiny, jacobi, sigma, with_mass):
     assert res.resnorm <= 1e-12 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("sigma", [-151.5, -300.0 + 200.0j])
+def test_bicgstab_step_conditions(tiny, sigma):
+    """The two conditions that define a BiCGstab step (van der Vorst 1992):
+    alpha makes the intermediate residual s = r - alpha v orthogonal to the
+    shadow vector (rhat^* s = 0, the BiCG condition), and omega minimises
+    ||s - omega t||, so the new residual is orthogonal to t (t^* r = 0).  A
+    conjugation slip in either coefficient breaks one of them for a complex
+    shift, although the iteration may still converge."""
+    S = tiny.A.to_scipy()
+    b = W.normal(11, 0, 0, tiny.A.n).astype(complex)
+    steps = []
+    res = bicgstab(S, sigma, b, 1e-12, jacobi=True, trace=steps.append)
+    assert res.converged and len(steps) >= 5
+    for st in steps:
+        rh, s, t, r = st["rhat"], st["s"], st["t"], st["r"]
+        assert abs(np.vdot(rh, s)) <= 1e-10 * np.linalg.norm(rh) * np.linalg.norm(s)
+        assert abs(np.vdot(t, r)) <= 1e-10 * np.linalg.norm(t) * np.linalg.norm(r)
+
+
 def test_bicgstab_multiple_of_identity_takes_one_step():
     """Op = c I: p = r, v = (c + sigma) r, alpha = 1 / (c + sigma), s = 0:
     one step gives x = b / (c + sigma) (up to rounding)."""
