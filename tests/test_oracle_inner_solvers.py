@@ -76,6 +76,23 @@ def test_bicgstab_step_conditions(tiny, sigma):
         assert abs(np.vdot(t, r)) <= 1e-10 * np.linalg.norm(t) * np.linalg.norm(r)
 
 
+@pytest.mark.parametrize("n", [5, 6, 8])
+@pytest.mark.parametrize("sigma", [0.5, 1.0 + 0.7j])
+def test_bicgstab_terminates_in_n_steps(n, sigma):
+    """In exact arithmetic BiCGstab's residual is the BiCG residual times a
+    product of first-degree factors, and BiCG terminates after at most n
+    steps, so on a small nonsymmetric system (distinct eigenvalues, no
+    breakdown) the recurrence residual drops to rounding level exactly at step
+    n.  A wrong search direction (beta or the q = p - omega v correction)
+    loses this."""
+    M = np.diag(2.0 * np.arange(1, n + 1)) + 0.3 * W.normal(21, 1, 0, n * n).reshape(n, n)
+    b = W.normal(21, 2, 0, n).astype(complex)
+    nb = np.linalg.norm(b)
+    res = bicgstab(sp.csr_matrix(M), sigma, b, 1e-12 * nb, max_iters=3 * n)
+    assert res.converged and res.iters == n and res.cycles == 1
+    assert res.history[n - 2] > 1e-8 * nb and res.history[n - 1] <= 1e-13 * nb
+
+
 def test_bicgstab_multiple_of_identity_takes_one_step():
     """Op = c I: p = r, v = (c + sigma) r, alpha = 1 / (c + sigma), s = 0:
     one step gives x = b / (c + sigma) (up to rounding)."""
