@@ -190,6 +190,41 @@ def test_theorem1_and_2_inexact(tiny):
     assert gap <= res.history[-1]["u"] + res.history[-1]["v"] + 1e-20
 
 
+def test_lowrank_norms_match_dense_complex():
+    """The factored norms with complex factors and a complex core (conjugate
+    transposes, not transposes): ||U W^*||_2 and the residual of
+    X = Z diag(gamma) Y^* against the dense matrices."""
+    rng = np.random.default_rng(9)
+    U = rng.standard_normal((30, 3)) + 1j * rng.standard_normal((30, 3))
+    V = rng.standard_normal((20, 3)) + 1j * rng.standard_normal((20, 3))
+    assert lowrank_norm2(U, V) == pytest.approx(np.linalg.norm(U @ V.conj().T, 2), rel=1e-12)
+    assert lowrank_fro(U, V) == pytest.approx(np.linalg.norm(U @ V.conj().T), rel=1e-12)
+    n, m, k, r = 12, 9, 4, 2
+    A = sp.csr_matrix(rng.standard_normal((n, n)))
+    B = sp.csr_matrix(rng.standard_normal((m, m)))
+    f, g = rng.standard_normal((n, r)), rng.standard_normal((m, r))
+    Z = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    Y = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    gam = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    X = (Z * gam[None, :]) @ Y.conj().T
+    R = A @ X + X @ B + f @ g.conj().T
+    assert true_residual_norm2(A, B, f, g, Z, gam, Y) == pytest.approx(np.linalg.norm(R, 2), rel=1e-10)
+
+
+def test_inner_solves_meet_the_per_column_target(tiny):
+    """Sec. 3.3: each of the r column systems of a step is solved to
+    delta_k / r (so that the n x r block residual meets delta_k); the stored
+    inner residuals of every converged solve satisfy it column by column."""
+    r = tiny.r
+    res = lradi(tiny.A, tiny.B, tiny.f, tiny.g, tiny.alpha, tiny.beta, tiny.tau, strategy="nobl_mid",
+                keep_inner_residuals=True)
+    for k, h in enumerate(res.history):
+        for S, d, ok in ((res.S_A, h["dA"], h["okA"]), (res.S_B, h["dB"], h["okB"])):
+            assert ok
+            cols = np.linalg.norm(S[:, k * r:(k + 1) * r], axis=0)
+            assert np.all(cols <= d / r * (1 + 1e-10)), (k, cols, d / r)
+
+
 def test_sampled_residual_matches_dense(tiny):
     from oracle.residual import sampled_residual
     res = lradi(tiny.A, tiny.B, tiny.f, tiny.g, tiny.alpha, tiny.beta, tiny.tau, strategy="bl_mid", kmax=4)
