@@ -290,6 +290,33 @@ def test_back_looking_target_beyond_the_first_step():
     assert eh == pytest.approx(7.699964106250138e-11, rel=1e-13)
 
 
+def test_selection_rules_hand_values():
+    """eq. (simple_tols), eq. (one_side) and its mirror, and the fixed rule
+    with a directly solved side, on numbers worked by hand (hat-eps = 1e-6,
+    ||w|| = 2, ||t|| = 4, delta_max = 0.1)."""
+    e, Nw, Nt = 1e-6, 2.0, 4.0
+    # mid, delta_min = 5e-8 on both sides: delta^A = (min(0.1, 1e-6 / 4) - 5e-8) / 2
+    # = (2.5e-7 - 5e-8) / 2 = 1e-7 (the literal midpoint: minus delta_min);
+    # delta^B on the curve: (1e-6 - 1e-7 * 4) / (2 * 1e-7 + 2) = 6e-7 / 2.0000002
+    # = 2.99999970000003e-7
+    dA, dB = ctl.select_mid(e, Nw, Nt, 5e-8, 0.1, 5e-8, 0.1)
+    assert dA == pytest.approx(1e-7, rel=1e-14)
+    assert dB == pytest.approx(2.9999997000000295e-07, rel=1e-13)
+    # B preferred, delta^A_min = 3e-7, delta^B_min = 1e-9: delta^B = 1e-9; delta^A on
+    # the curve (1e-6 - 1e-9 * 2) / (2e-9 + 4) = 2.49499999875e-7, below
+    # delta^A_min, so the clamp of eq. (bound_tols) on the A side gives 3e-7
+    dA, dB = ctl.select_prefer_B(e, Nw, Nt, 3e-7, 0.1, 1e-9, 0.1)
+    assert dB == 1e-9 and dA == pytest.approx(3e-7, rel=1e-15)
+    dA, dB = ctl.select_prefer_B(e, Nw, Nt, 1e-9, 0.1, 1e-9, 0.1)
+    assert dA == pytest.approx(2.4949999987525e-07, rel=1e-13)
+    # fixed tolerances with one side solved directly: that side's tolerance is 0
+    kw = dict(k=3, kmax=50, eps=1e-8, xi=1.0, u_prev=0.0, v_prev=0.0, N_w=Nw, N_t=Nt, dmin_A=1e-9,
+              dmax_A=0.1, dmin_B=1e-9, dmax_B=0.1, fixed_tol=5e-10)
+    assert ctl.inner_tolerances("fixed", direct="A", **kw)[:2] == (0.0, 5e-10)
+    assert ctl.inner_tolerances("fixed", direct="B", **kw)[:2] == (5e-10, 0.0)
+    assert ctl.inner_tolerances("fixed", **kw)[:2] == (5e-10, 5e-10)
+
+
 def test_fig1_axis_values():
     """Fig. 1 (c = 3, eps = 1e-8, ||t|| = 1e-5, ||w|| = 2e-3): the curve
     Psi = 0 meets the axes at eps/(c ||w||) and eps/(c ||t||)."""
