@@ -126,6 +126,38 @@ def test_inexact_real_formulation(t3d, inner):
     assert rr.complex_solves < 2 * rr.steps * p.r
 
 
+@pytest.mark.parametrize("complex_alpha,complex_beta", [(False, True), (True, False)])
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+def test_inexact_pairs_meet_the_column_targets(tiny, complex_alpha, complex_beta, inner):
+    """With one side's shift of the pair real (two real solves there, to
+    delta / 2 and delta / (2 |gamma|)) and the other complex (one complex
+    solve to delta / (1 + |gamma| / |Im shift|)): every column of every step of
+    the equivalent complex formulation, the derived second ones included,
+    meets the per-column target delta / r of the pair's controller evaluation
+    (Sec. 3.3), and u, v accumulate eq. (upd_resgap) over both steps of each
+    pair."""
+    al, be = _pairs(tiny, complex_alpha, complex_beta)
+    r = tiny.r
+    rr = lradi_real(tiny.A, tiny.B, tiny.f, tiny.g, al, be, 1e-8, inner=inner, strategy="nobl_mid",
+                    keep_inner_residuals=True, kmax=30)
+    assert rr.converged
+    j = 0
+    u = v = 0.0
+    for h in rr.history:
+        for _ in range(2 if h["pair"] else 1):
+            st = rr.steps_complex[j]
+            j += 1
+            ca = np.linalg.norm(st["rA"], axis=0)
+            cb = np.linalg.norm(st["rB"], axis=0)
+            assert np.all(ca <= h["dA"] / r * (1 + 1e-9)), (h["k"], ca, h["dA"] / r)
+            assert np.all(cb <= h["dB"] / r * (1 + 1e-9)), (h["k"], cb, h["dB"] / r)
+            g = abs(st["gamma"])
+            u += g * np.linalg.norm(st["z"], 2) * np.linalg.norm(st["rB"], 2)
+            v += g * np.linalg.norm(st["y"], 2) * np.linalg.norm(st["rA"], 2)
+        assert h["u"] == pytest.approx(u, rel=1e-10) and h["v"] == pytest.approx(v, rel=1e-10)
+    assert j == len(rr.steps_complex)
+
+
 def test_unpaired_complex_shift_is_rejected(tiny):
     al = np.array([-100.0 + 50j, -200.0])
     be = np.array([-80.0, -90.0])
