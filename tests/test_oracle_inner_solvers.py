@@ -93,6 +93,24 @@ def test_bicgstab_terminates_in_n_steps(n, sigma):
     assert res.history[n - 2] > 1e-8 * nb and res.history[n - 1] <= 1e-13 * nb
 
 
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+def test_jacobi_of_the_shifted_pencil(solver):
+    """Right Jacobi for (Op + sigma Mass) x = b divides by the diagonal of the
+    pencil, diag(Op) + sigma diag(Mass): when Op and Mass are diagonal the
+    preconditioned operator is the identity and one step solves the system
+    exactly (a preconditioner built from diag(Op) + sigma alone would not)."""
+    n = 40
+    d1 = 1.0 + np.arange(n, dtype=float)
+    d2 = 0.5 + 0.25 * np.arange(n, dtype=float)
+    S, Mass = sp.diags(d1).tocsr(), sp.diags(d2).tocsr()
+    b = W.normal(17, 0, 0, n)
+    sigma = 3.0
+    f = gmres if solver == "gmres" else bicgstab
+    res = f(S, sigma, b, 1e-12 * np.linalg.norm(b), jacobi=True, mass=Mass)
+    assert res.converged and res.iters == 1
+    assert np.allclose(res.x, b / (d1 + sigma * d2), rtol=1e-13)
+
+
 def test_bicgstab_multiple_of_identity_takes_one_step():
     """Op = c I: p = r, v = (c + sigma) r, alpha = 1 / (c + sigma), s = 0:
     one step gives x = b / (c + sigma) (up to rounding)."""
