@@ -18,6 +18,7 @@ from paper_2312_02891_gb300 import workloads as W
 from oracle.dense import bartels_stewart, dense_residual, kron_solve
 from oracle.gmres import gmres
 from oracle.lradi import lradi
+from oracle.lradi_real import lradi_real
 from oracle.residual import block_norm2, true_residual_norm2
 
 
@@ -120,6 +121,31 @@ def test_generalized_lradi_converges_to_dense_solution(micro_g, inner, strategy)
     if inner == "direct":
         r0 = lradi(p.A, p.B, p.f, p.g, p.alpha, p.beta, p.tau, inner=inner, kmax=60)
         assert np.linalg.norm(X_of(r0) - Xd) > 1e-2 * np.linalg.norm(Xd)
+
+
+@pytest.mark.parametrize("real_pairs", [False, True])
+def test_generalized_nonsymmetric_mass_matrices(micro_g, real_pairs):
+    """eq. (gsylv) with nonsymmetric M and C (the Q1 mass matrices plus a
+    strictly lower part), so that every transpose and conjugate transpose of
+    C and M in Algorithm 1 matters (the B-side systems use (B + alpha C)^*):
+    with exact solves the factored X matches the Kronecker solution."""
+    pr = micro_g
+    A, B, M, C = mats(pr)
+    M2 = (M + 0.3 * sp.tril(M, -1)).tocsr()
+    C2 = (C + 0.3 * sp.tril(C, -1)).tocsr()
+    Xd = kron_solve(A, B, pr.f, pr.g, M2, C2)
+    if real_pairs:
+        res = lradi_real(pr.A, pr.B, pr.f, pr.g, pr.alpha, pr.beta, pr.tau, M=M2, C=C2, inner="direct",
+                         strategy="fixed", kmax=60)
+        X = res.Z @ res.Gamma @ res.Y.T
+    else:
+        res = lradi(pr.A, pr.B, pr.f, pr.g, pr.alpha, pr.beta, pr.tau, M=M2, C=C2, inner="direct",
+                    strategy="fixed", kmax=60)
+        X = X_of(res)
+    assert res.converged
+    assert np.linalg.norm(X - Xd) <= 1e-6 * np.linalg.norm(Xd)
+    R = dense_residual(A, B, pr.f, pr.g, X, M2, C2)
+    assert np.linalg.norm(R, 2) <= 3 * pr.tau * np.linalg.norm(pr.f @ pr.g.T, 2)
 
 
 def test_generalized_residual_factorisation_exact_solves(tiny_g):
