@@ -290,6 +290,20 @@ def test_back_looking_target_beyond_the_first_step():
     assert eh == pytest.approx(7.699964106250138e-11, rel=1e-13)
 
 
+def test_pair_detection():
+    """A conjugate pair is a shift (alpha, beta), not both real, followed by
+    (conj alpha, conj beta): both members must be conjugate, and the last
+    shift of the list opens no pair."""
+    from oracle.lradi import _is_pair_start
+    a = np.array([-1 + 2j, -1 - 2j, -3.0, -3.0])
+    assert _is_pair_start(a, np.array([-2 + 1j, -2 - 1j, -4.0, -4.0]), 0)
+    assert _is_pair_start(a, np.array([-2.0, -2.0, -4.0, -4.0]), 0)       # real beta, complex alpha
+    assert not _is_pair_start(a, np.array([-2 + 1j, -2 + 1j, -4.0, -4.0]), 0)
+    assert not _is_pair_start(a, np.array([-2.0, -5.0, -4.0, -4.0]), 0)
+    assert not _is_pair_start(a, np.array([-2.0, -2.0, -4.0, -4.0]), 2)   # both real
+    assert not _is_pair_start(np.array([-1.0, -1 + 2j]), np.array([-2.0, -2 + 1j]), 1)
+
+
 def test_selection_rules_hand_values():
     """eq. (simple_tols), eq. (one_side) and its mirror, and the fixed rule
     with a directly solved side, on numbers worked by hand (hat-eps = 1e-6,
