@@ -126,7 +126,7 @@ def test_inexact_real_formulation(t3d, inner):
     assert rr.complex_solves < 2 * rr.steps * p.r
 
 
-@pytest.mark.parametrize("complex_alpha,complex_beta", [(False, True), (True, False)])
+@pytest.mark.parametrize("complex_alpha,complex_beta", [(False, True), (True, False), (None, None)])
 @pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
 def test_inexact_pairs_meet_the_column_targets(tiny, complex_alpha, complex_beta, inner):
     """With one side's shift of the pair real (two real solves there, to
@@ -136,10 +136,19 @@ def test_inexact_pairs_meet_the_column_targets(tiny, complex_alpha, complex_beta
     meets the per-column target delta / r of the pair's controller evaluation
     (Sec. 3.3), and u, v accumulate eq. (upd_resgap) over both steps of each
     pair."""
-    al, be = _pairs(tiny, complex_alpha, complex_beta)
+    if complex_alpha is None:
+        # real steps between the pairs: the problem's real shifts with one
+        # complex-beta pair inserted after the first two
+        a, b = np.real(tiny.alpha), np.real(tiny.beta)
+        al = np.array([a[0], a[1], a[2], a[2]] + list(a[3:]), dtype=complex)
+        be = np.array([b[0], b[1], b[2] + 0.2j * abs(b[2]), b[2] - 0.2j * abs(b[2])] + list(b[3:]))
+    else:
+        al, be = _pairs(tiny, complex_alpha, complex_beta)
     r = tiny.r
     rr = lradi_real(tiny.A, tiny.B, tiny.f, tiny.g, al, be, 1e-8, inner=inner, strategy="nobl_mid",
                     keep_inner_residuals=True, kmax=30)
+    if complex_alpha is None:
+        assert any(h["pair"] for h in rr.history) and any(not h["pair"] for h in rr.history)
     assert rr.converged
     j = 0
     u = v = 0.0
