@@ -520,17 +520,27 @@ def test_dcgs2_arnoldi_relation_and_orthonormality(sigma):
     assert np.all(H[np.arange(1, k + 1), np.arange(k)].real > 0)
 
 
-def test_dcgs2_gmres_matches_cgs2_gmres(small):
+@pytest.mark.parametrize("cplx", [False, True])
+def test_dcgs2_gmres_matches_cgs2_gmres(small, cplx):
     """Same Krylov spaces in exact arithmetic: the delayed variant takes the
     same number of steps and returns the same solution as CGS2 (small2d
-    A-side system, with and without Jacobi)."""
+    A-side system, with and without Jacobi, real and complex shift), and both
+    match the sparse LU solution (a conjugation slip in either Givens update
+    breaks the complex case)."""
     S = small.A.to_scipy()
+    sig = small.beta[0] + (0.3j * abs(small.beta[0]) if cplx else 0.0)
+    rhs = small.f[:, 0].astype(complex) if cplx else small.f[:, 0]
+    x_lu = spla.spsolve((S + sig * sp.identity(S.shape[0])).tocsc(), rhs)
     for jac in (False, True):
-        a = gmres(S, small.beta[0], small.f[:, 0], 1e-10, 30, 3000, jac, "cgs2")
-        b = gmres(S, small.beta[0], small.f[:, 0], 1e-10, 30, 3000, jac, "dcgs2")
+        a = gmres(S, sig, rhs, 1e-10, 30, 3000, jac, "cgs2")
+        b = gmres(S, sig, rhs, 1e-10, 30, 3000, jac, "dcgs2")
         assert a.converged and b.converged and a.iters == b.iters and a.cycles == b.cycles
         assert np.linalg.norm(a.x - b.x) <= 1e-12 * np.linalg.norm(a.x)
         assert np.allclose(a.history, b.history, rtol=1e-6)
+        assert np.linalg.norm(a.x - x_lu) <= 1e-6 * np.linalg.norm(x_lu)
+        # the Givens estimates are the true residual norms of the GMRES
+        # iterates (right preconditioning): the last one below the tolerance
+        assert a.history[-1] <= 1e-10 and b.history[-1] <= 1e-10
 
 
 def test_dcgs2_gmres_diagonal_operator_exact_steps():
