@@ -135,12 +135,13 @@ typedef struct sylv_opts {
                                     with 2 x 2 blocks (sylv_adi_core).  Runs the host-driven loop;
                                     not built for batches with complex shifts. */
     int32_t autotune;            /* with rows_per_chunk = 0: 1 times a bounded set of work-chunk
-                                    sizes (the one-wave rule and 512 .. 8192 rows) on the actual
-                                    systems at create - synthetic vectors and a stencil of the
-                                    operators' shape, CUDA events over a few device iterations -
-                                    and keeps the fastest (sylv_adi_tuning reports them); 0 (the
-                                    default) uses the one-wave rule, so that results do not
-                                    depend on timing */
+                                    sizes (the default rule's size and 512 .. 8192 rows) on the
+                                    actual systems at create - synthetic vectors and a stencil of
+                                    the operators' shape, CUDA events over a few device
+                                    iterations - and keeps the fastest (sylv_adi_tuning reports
+                                    them); 0 (the default) uses the default rule, so that results
+                                    do not depend on timing: GMRES one wave of resident blocks
+                                    over all rows, BiCGstab at most 768 rows (at least 256) */
 } sylv_opts;
 
 #define SYLV_INNER_GMRES     0
