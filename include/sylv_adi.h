@@ -86,7 +86,8 @@ typedef struct sylv_opts {
     int32_t restart;             /* GMRES restart length m, 1..SYLV_MAX_RESTART */
     int32_t max_inner;           /* cap on Arnoldi steps per column solve */
     int32_t precision;           /* SYLV_PREC_* */
-    int32_t jacobi;              /* 1: right preconditioner P = diag(Op) + shift */
+    int32_t jacobi;              /* 1: right preconditioner P = diag(Op) + shift diag(Mass)
+                                    (Mass = I unless the generalized equation gives one) */
     int32_t bl_clamp;            /* 0: eq. (ADI_relax2_prak) literally, |.|;
                                     1: max(., 0) in place of |.| (paper silent) */
     int32_t rows_per_chunk;      /* work-unit size of the vector kernels; 0 = auto */
