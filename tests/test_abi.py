@@ -95,3 +95,34 @@ def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mod.load()
     importlib.reload(P)
+
+
+def test_noalloc_entry_point_refuses_bad_sizes_without_gpu(lib):
+    """The allocation-free CGS2 step checks its sizes before any device call:
+    rows beyond what its static scratch holds, a basis size outside
+    1..restart and null pointers are refused with a message.  The pointers
+    given here are never dereferenced (the call returns first)."""
+    mx = P.sylv_cgs2_noalloc_max_rows()
+    assert mx > 100000
+    h = np.zeros(8)
+    hp = h.ctypes.data_as(C.POINTER(C.c_double))
+    fake = C.c_void_p(16)
+    assert lib.sylv_cgs2_noalloc(fake, mx + 1, 5, fake, hp, None) == -1
+    assert "static scratch" in P.sylv_last_error()
+    assert lib.sylv_cgs2_noalloc(fake, 1000, 0, fake, hp, None) == -1
+    assert lib.sylv_cgs2_noalloc(fake, 1000, 31, fake, hp, None) == -1
+    assert lib.sylv_cgs2_noalloc(None, 1000, 5, fake, hp, None) == -1
+    assert lib.sylv_cgs2_noalloc(fake, 0, 5, fake, hp, None) == -1
+
+
+def test_noalloc_binding_checks_its_tensors():
+    """The binding refuses tensors the library must not write into before
+    it calls the library: host tensors and other dtypes (the refusal of
+    device buffers smaller than n x (k + 1) or n needs device tensors)."""
+    torch = pytest.importorskip("torch")
+    n, k = 64, 3
+    v = torch.zeros(n * (k + 1), dtype=torch.float64)
+    w = torch.zeros(n, dtype=torch.float64)
+    for V, W_ in ((v, w), (v.float(), w), (v, w.float())):
+        with pytest.raises(P.SylvError, match="contiguous float64 CUDA tensor"):
+            P.sylv_cgs2_noalloc(V, n, k, W_)
